@@ -1,0 +1,169 @@
+/*
+ * isam.h -- C ABI of the GB300 (sm_103a) full-range dispersion-encoded ISAM
+ * library: the forward model, its adjoint and the weighted-l1 MBIR solve of
+ * Mason, Davies & Bagnaninchi, "Blur resolved OCT: full-range ISAM through
+ * dispersion encoding" (arXiv 1905.06058).
+ *
+ * Model (paper §2-§3):
+ *   s = A eta = Re( diag(e^{j phi}) K eta )                       Eq. (12)-(13)
+ *   K = F_lat^{-1} o [Stolt-mapped axial transform, min-max NUFFT] o F_lat
+ *                                                                  Eq. (3), (16)
+ *   phi(k) = sum_{i=1..n_disp} a_i (k - k0)^i                      Eq. (7)
+ *   A^H y = F_lat^{-1} N'( conj(e^{j phi}) F_lat y )               Eq. (17)
+ *   eta~ = argmin 1/2 ||A eta - s_d||^2 + lambda w^T |eta|         Eq. (12)
+ *   solved by FISTA with weighted complex soft threshold            Alg. 1, Eq. (14)
+ *   and the relative-residual stop rule                             Eq. (15)
+ *
+ * Conventions (the paper leaves them open; they are fixed here):
+ *   k_j = k_min + j dk, j < nk, dk = (k_max - k_min)/(nk - 1), k0 = (k_min+k_max)/2
+ *   z_n = (n - nz/2) dz, dz = pi / (nz dk)   (full complex range pi/dk)
+ *   q   = 2 pi fftfreq(nx, dx) (and ny, dy); lateral FFTs are unitary;
+ *   the axial transform carries 1/sqrt(nz) and the focus phase e^{j(2k+beta)z0},
+ *   beta = -sqrt(4k^2 - q^2); samples with 4k^2 <= q^2 are zero in A and ignored in A^H;
+ *   NUFFT: oversampling K = 2 nz, J-neighbour min-max interpolation (J = 4, 6 or 8)
+ *   with Kaiser-Bessel-shaped scaling (alpha = 2.34 J) over the design set
+ *   n' = -nz/2..nz/2; FISTA uses step 1/L and threshold lambda w / L, L = ||A||^2.
+ *
+ * Layouts (row-major, last index fastest), element types by plan precision:
+ *   image eta : complex [ny][nx][nz]  (interleaved re,im; float2 or double2)
+ *   spectra s : real    [ny][nx][nk]  (float or double), A-scans contiguous
+ *   weights w : real    [nz]          (per image row, broadcast over x, y)
+ *
+ * Ownership and threading: the caller owns every buffer passed in; a plan owns
+ * its device workspace and tables.  Calls are asynchronous on the plan's
+ * stream unless stated; device pointers must be valid CUDA device (or managed)
+ * memory of the plan's device.  Errors found before launch are returned
+ * immediately; a CUDA launch failure returns ISAM_ERR_CUDA.  A plan may be
+ * used by one host thread at a time; distinct plans are independent.
+ */
+#ifndef ISAM_H
+#define ISAM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ISAM_OK = 0,
+  ISAM_ERR_INVALID = 1,     /* bad argument (null pointer, size, range)     */
+  ISAM_ERR_OOM = 2,         /* device allocation failed                     */
+  ISAM_ERR_CUDA = 3,        /* a CUDA call or kernel launch failed          */
+  ISAM_ERR_NONFINITE = 4,   /* the solve produced a NaN or Inf              */
+  ISAM_ERR_TIMEOUT = 5,     /* a bounded device wait expired                */
+  ISAM_ERR_UNSUPPORTED = 6  /* valid but not implemented (size, J, os)      */
+} isam_status;
+
+enum { ISAM_FP32 = 0, ISAM_FP64 = 1 };
+
+/* Acquisition geometry and numerics: the problem as the paper states it
+ * (spectral samples, lateral grid, NA and focus, dispersion; §2, §4.1). */
+typedef struct {
+  int32_t nx, ny;      /* lateral samples (powers of two, 1..4096); ny = 1: B-scan */
+  int32_t nk;          /* spectral samples per A-scan (power of two, 16..4096)      */
+  int32_t nz;          /* depth samples of the image (power of two, >= 16); 0: nk   */
+  double k_min, k_max; /* band edges, rad/m (k_max > k_min > 0)                     */
+  double dx, dy;       /* lateral pitch, m (dy ignored when ny = 1)                 */
+  double na;           /* numerical aperture (recorded; the unfiltered model, b = 1) */
+  double z0;           /* focal depth on the z grid, m (Stolt origin)               */
+  int32_t n_disp;      /* number of dispersion coefficients used (0..4)             */
+  double disp[4];      /* a_1..a_4, rad m^i, about k0 (Eq. 7)                       */
+  int32_t precision;   /* ISAM_FP32 or ISAM_FP64                                    */
+  int32_t nufft_J;     /* interpolation neighbours: 4, 6 or 8 (0: 6)               */
+  int32_t nufft_os;    /* oversampling factor: 2 (0: 2)                            */
+} isam_params;
+
+typedef struct isam_plan isam_plan;
+
+/* Options of the MBIR solve (Alg. 1, §3.1). */
+typedef struct {
+  double lambda_rel;        /* lambda = lambda_rel * ||A^H s_d||_inf ...          */
+  double lambda_abs;        /* ... unless lambda_abs > 0, which is used as is     */
+  int32_t max_iter;         /* FISTA iterations (>= 1)                            */
+  double tol;               /* stop when r_r < tol (Eq. 15); 0 disables the rule  */
+  int32_t check_every;      /* iterations between stop-rule evaluations (>= 1)    */
+  const void* w_dev;        /* nullable device [nz] weights w (real, plan type)   */
+  int32_t residual_addback; /* 1: return z + (1/L) A^H (s_d - A z) (Alg. 1 end)   */
+  double L;                 /* step 1/L; 0: power-iteration estimate, cached      */
+  double eps;               /* r_r denominator guard (0: 1e-30)                   */
+} isam_solve_opts;
+
+/* Resumable solver state (checkpoint/restart).  z1 = z^{k}, z2 = z^{k-1} are
+ * caller-owned device images; k iterations are done.  Pass k = 0 to start. */
+typedef struct {
+  void* z1;
+  void* z2;
+  int32_t k;
+  double lambda;
+  double L;
+} isam_solve_state;
+
+typedef struct {
+  int32_t iterations;  /* iterations performed by this call                   */
+  double rr;           /* last evaluated relative residual (-1 if never)      */
+  double lambda;       /* regularisation used                                 */
+  double L;            /* Lipschitz constant used                             */
+  int32_t status;      /* isam_status of the solve                            */
+} isam_solve_info;
+
+/* Create a plan: validates p, builds the NUFFT tables (FP64 on the device),
+ * allocates workspace on the current device, binds `stream` (a cudaStream_t,
+ * NULL for the legacy default stream).  Synchronous.  *out is NULL on error. */
+isam_status isam_plan_create(const isam_params* p, void* stream, isam_plan** out);
+void isam_plan_destroy(isam_plan* plan);
+isam_status isam_set_stream(isam_plan* plan, void* stream);
+
+/* s = A eta (Eq. 12-13, 16).  eta: device image, s: device spectra. */
+isam_status isam_forward(isam_plan* plan, const void* eta, void* s);
+
+/* eta = A^H s (Eq. 17), exact adjoint of isam_forward under <a,b> = Re(a^H b). */
+isam_status isam_adjoint(isam_plan* plan, const void* s, void* eta);
+
+/* MBIR solve (Alg. 1): s_d device spectra -> eta_out device image.  Synchronises
+ * the plan's stream before returning (it reads back the stop rule and status).
+ * state may be NULL. info may be NULL. */
+isam_status isam_solve(isam_plan* plan, const void* s_d, const isam_solve_opts* opts,
+                       void* eta_out, isam_solve_state* state, isam_solve_info* info);
+
+/* The same solve with host buffers: copies s_d in, solves, copies eta out. */
+isam_status isam_solve_host(isam_plan* plan, const void* s_d_host,
+                            const isam_solve_opts* opts, void* eta_out_host,
+                            isam_solve_info* info);
+
+/* L = ||A^H A|| by power iteration from the device start image v0 (NULL: a fixed
+ * deterministic start), in FP64 on the device whatever the plan precision.
+ * Synchronous.  The result is cached in the plan and used by isam_solve. */
+isam_status isam_lipschitz(isam_plan* plan, int32_t iters, double rtol, const void* v0,
+                           double* L_out);
+
+/* max |eta_i| of a device image (used for lambda = c ||A^H s||_inf).  Synchronous. */
+isam_status isam_max_abs(isam_plan* plan, const void* eta, double* out);
+
+/* Kernel launches issued by the last isam_forward / isam_adjoint / isam_solve. */
+int64_t isam_last_launch_count(const isam_plan* plan);
+
+/* Optional per-kernel timing: while enabled, every kernel launch of the plan is
+ * bracketed by CUDA events on the plan's stream and its device time is added to
+ * one of these classes.  Measurement support; not part of the method. */
+enum {
+  ISAM_KCLASS_AX_FWD = 0,      /* Stolt NUFFT forward (axial)               */
+  ISAM_KCLASS_AX_ADJ = 1,      /* Stolt NUFFT adjoint (axial)               */
+  ISAM_KCLASS_LAT_MID = 2,     /* fused lateral IFFT, Re, -s_d, FFT         */
+  ISAM_KCLASS_LAT_UPDATE = 3,  /* fused lateral IFFT, FISTA step, FFT       */
+  ISAM_KCLASS_LAT_FFT = 4,     /* plain lateral FFT passes                  */
+  ISAM_KCLASS_MISC = 5,        /* reductions and elementwise kernels        */
+  ISAM_KCLASS_COUNT = 6
+};
+/* Enable (1) or disable (0) the timing; synchronises the plan's stream. */
+isam_status isam_profile_enable(isam_plan* plan, int32_t on);
+/* Synchronise the stream, then copy accumulated milliseconds and launch counts
+ * per class into ms[ISAM_KCLASS_COUNT], counts[ISAM_KCLASS_COUNT]; reset if asked. */
+isam_status isam_profile_read(isam_plan* plan, double* ms, int64_t* counts, int32_t reset);
+
+const char* isam_status_string(isam_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ISAM_H */

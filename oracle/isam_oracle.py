@@ -196,11 +196,14 @@ def grid_position(beta: np.ndarray, dz: float, K: int) -> np.ndarray:
     return -beta * dz * K / (2 * math.pi)
 
 
-def nufft_forward_column(x: np.ndarray, p: np.ndarray, interp: MinMaxInterpolator) -> np.ndarray:
+def nufft_forward_column(x: np.ndarray, p: np.ndarray, interp: MinMaxInterpolator,
+                         c: Optional[np.ndarray] = None) -> np.ndarray:
     """X(p_j) ~= sum_n x_n e^{j 2 pi p_j (n - nz/2) / K}, min-max NUFFT.
 
     Steps: scale by s, zero-pad to K with sample n at n - nz/2 mod K,
-    K-point DFT with e^{+j}, J-neighbour interpolation.
+    K-point DFT with e^{+j}, J-neighbour interpolation.  ``c`` optionally
+    passes the coefficients of these positions, computed earlier by
+    ``interp.coefficients`` (a memo; the arithmetic is the same).
     """
     nz, K, J = interp.nz, interp.K, interp.J
     v = np.zeros(K, np.complex128)
@@ -210,20 +213,23 @@ def nufft_forward_column(x: np.ndarray, p: np.ndarray, interp: MinMaxInterpolato
     fl = np.floor(p)
     f = p - fl
     m0 = fl.astype(np.int64) - J // 2 + 1
-    c = interp.coefficients(f)
+    if c is None:
+        c = interp.coefficients(f)
     out = np.zeros(p.shape, np.complex128)
     for l in range(J):
         out += c[:, l] * Y[(m0 + l) % K]
     return out
 
 
-def nufft_adjoint_column(y: np.ndarray, p: np.ndarray, interp: MinMaxInterpolator) -> np.ndarray:
+def nufft_adjoint_column(y: np.ndarray, p: np.ndarray, interp: MinMaxInterpolator,
+                         c: Optional[np.ndarray] = None) -> np.ndarray:
     """Exact adjoint of ``nufft_forward_column`` (ISAM back-projection, Eq. 17)."""
     nz, K, J = interp.nz, interp.K, interp.J
     fl = np.floor(p)
     f = p - fl
     m0 = fl.astype(np.int64) - J // 2 + 1
-    c = interp.coefficients(f)
+    if c is None:
+        c = interp.coefficients(f)
     Yg = np.zeros(K, np.complex128)
     for l in range(J):
         np.add.at(Yg, (m0 + l) % K, c[:, l] * y)
@@ -272,6 +278,17 @@ class IsamOracle:
             cache[key] = E
         return E
 
+    def _coef(self, iy, ix):
+        """Min-max coefficients of one column's Stolt positions (memoised)."""
+        cache = self.__dict__.setdefault("_C", {})
+        if (iy, ix) in cache:
+            return cache[(iy, ix)]
+        p = self.p[iy, ix]
+        c = self.interp.coefficients(p - np.floor(p))
+        if self.grid.nx * self.grid.ny * c.size <= 50_000_000:
+            cache[(iy, ix)] = c
+        return c
+
     def _axial_exact_col(self, x, iy, ix):
         return self._nudft_matrix(iy, ix) @ x / math.sqrt(self.grid.nz)
 
@@ -291,7 +308,7 @@ class IsamOracle:
                     out[iy, ix] = self._axial_exact_col(x, iy, ix)
                 else:
                     out[iy, ix] = nufft_forward_column(x / math.sqrt(gr.nz), self.p[iy, ix],
-                                                       self.interp)
+                                                       self.interp, self._coef(iy, ix))
         return out * self.prop
 
     def axial_adjoint(self, y_hat: np.ndarray) -> np.ndarray:
@@ -304,8 +321,8 @@ class IsamOracle:
                 if self.mode == "exact":
                     out[iy, ix] = self._axial_exact_adj_col(y, iy, ix)
                 else:
-                    out[iy, ix] = nufft_adjoint_column(y, self.p[iy, ix], self.interp) / \
-                        math.sqrt(gr.nz)
+                    out[iy, ix] = nufft_adjoint_column(y, self.p[iy, ix], self.interp,
+                                                       self._coef(iy, ix)) / math.sqrt(gr.nz)
         return out
 
     # -- full operators -------------------------------------------------------

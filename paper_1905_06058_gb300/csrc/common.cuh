@@ -1,0 +1,90 @@
+// Common device helpers: complex arithmetic on float2/double2, float-float
+// ("double-single") arithmetic for the Stolt positions, launch checks.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace isam {
+
+template <typename T> struct cplx_t;
+template <> struct cplx_t<float> { using type = float2; };
+template <> struct cplx_t<double> { using type = double2; };
+template <typename T> using cplx = typename cplx_t<T>::type;
+
+template <typename T> __host__ __device__ __forceinline__ cplx<T> mk(T re, T im) {
+  cplx<T> r; r.x = re; r.y = im; return r;
+}
+template <typename C> __host__ __device__ __forceinline__ C cadd(C a, C b) { a.x += b.x; a.y += b.y; return a; }
+template <typename C> __host__ __device__ __forceinline__ C csub(C a, C b) { a.x -= b.x; a.y -= b.y; return a; }
+template <typename C> __host__ __device__ __forceinline__ C cmul(C a, C b) {
+  C r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
+}
+// a * conj(b)
+template <typename C> __host__ __device__ __forceinline__ C cmulc(C a, C b) {
+  C r; r.x = a.x * b.x + a.y * b.y; r.y = a.y * b.x - a.x * b.y; return r;
+}
+template <typename C, typename T> __host__ __device__ __forceinline__ C cscale(C a, T s) { a.x *= s; a.y *= s; return a; }
+template <typename C> __host__ __device__ __forceinline__ C cconj(C a) { a.y = -a.y; return a; }
+// multiply by sign * i   (sign = +1 or -1)
+template <int SIGN, typename C> __host__ __device__ __forceinline__ C cmul_i(C a) {
+  C r; r.x = -SIGN * a.y; r.y = SIGN * a.x; return r;
+}
+
+// ---------------------------------------------------------------------------
+// float-float arithmetic (Dekker / Knuth error-free transformations).  A value
+// is hi + lo with |lo| <= ulp(hi)/2; about 44 bits of significand.
+// ---------------------------------------------------------------------------
+struct ff { float hi, lo; };
+
+__device__ __forceinline__ ff ff_two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ ff ff_quick(float a, float b) {  // |a| >= |b|
+  float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ ff ff_two_prod(float a, float b) {
+  float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  ff s = ff_two_sum(a.hi, b.hi);
+  ff t = ff_two_sum(a.lo, b.lo);
+  s.lo = __fadd_rn(s.lo, t.hi);
+  s = ff_quick(s.hi, s.lo);
+  s.lo = __fadd_rn(s.lo, t.lo);
+  return ff_quick(s.hi, s.lo);
+}
+__device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff_neg(b)); }
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  ff p = ff_two_prod(a.hi, b.hi);
+  p.lo = __fmaf_rn(a.hi, b.lo, p.lo);
+  p.lo = __fmaf_rn(a.lo, b.hi, p.lo);
+  return ff_quick(p.hi, p.lo);
+}
+__device__ __forceinline__ ff ff_mul_f(ff a, float b) {
+  ff p = ff_two_prod(a.hi, b);
+  p.lo = __fmaf_rn(a.lo, b, p.lo);
+  return ff_quick(p.hi, p.lo);
+}
+__device__ __forceinline__ ff ff_sqrt(ff a) {  // a > 0
+  float r = __fsqrt_rn(a.hi);
+  float e = __fadd_rn(__fmaf_rn(-r, r, a.hi), a.lo);
+  return ff_quick(r, __fdiv_rn(e, __fmul_rn(2.0f, r)));
+}
+__device__ __forceinline__ ff ff_div(ff a, ff b) {
+  float q1 = __fdiv_rn(a.hi, b.hi);
+  ff r = ff_sub(a, ff_mul_f(b, q1));
+  float q2 = __fdiv_rn(r.hi, b.hi);
+  r = ff_sub(r, ff_mul_f(b, q2));
+  float q3 = __fdiv_rn(r.hi, b.hi);
+  ff q = ff_quick(q1, q2);
+  return ff_add(q, {q3, 0.0f});
+}
+
+}  // namespace isam

@@ -1,0 +1,108 @@
+// Internal structures shared by the kernel translation units and the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace isam {
+
+// Density of the min-max coefficient table: nodes f = i / TABLE_D, i <= TABLE_D.
+constexpr int TABLE_D = 1024;
+
+// Per-plan constants of the Stolt map in oversampled-grid units (K = 2 nz,
+// grid unit = dk):  p_j = sqrt(4 kappa_j^2 - a) with kappa_j = k_j / dk and
+// a = (q / dk)^2 = Qx mx^2 + Qy my^2.  Written as p_j = c0 + 2 j - d_j with
+// c0 = 2 kappa_0 mod K (I0 + f0) and d_j = a / (2 kappa_j + p_j) >= 0.  The
+// focus phase is e^{j 2 pi d_j zeta}, zeta = dk z0 / (2 pi).
+struct StoltConst {
+  // float-float copies for the FP32 path
+  float kap_hi, kap_lo;
+  float qx_hi, qx_lo, qy_hi, qy_lo;
+  float zeta_hi, zeta_lo;
+  float f0;
+  // double copies for the FP64 path
+  double kap, Qx, Qy, zeta, c0d;
+  int I0;
+  int K, logK, nx, ny, nk, nz, J;
+  int focus;      // z0 != 0
+};
+
+template <typename T> struct Tables {
+  cplx<T>* tw_x = nullptr;   // [nx]  e^{-2 pi i m / nx}
+  cplx<T>* tw_y = nullptr;   // [ny]
+  cplx<T>* tw_K = nullptr;   // [K]
+  T* scale = nullptr;        // [nz]  s(n - nz/2) / sqrt(nz)
+  cplx<T>* disp = nullptr;   // [nk]  e^{j phi(k_j)}
+  T* coef = nullptr;         // [(TABLE_D+1)][2J]  c_l(f_i), then c_l(f_{i+1}) - c_l(f_i)
+};
+
+// Lateral pass modes.
+enum LatMode : int {
+  LAT_C2C_FWD = 0,   // X = F x
+  LAT_C2C_INV = 1,   // X = F^-1 x
+  LAT_R2C_FWD = 2,   // real input, X = F x
+  LAT_INV_REAL = 3,  // real output, Re(F^-1 x)
+  LAT_MID = 4,       // R = F( Re(F^-1 S) - s_d )
+  LAT_UPDATE = 5,    // FISTA step in image space between F^-1 and F
+};
+
+template <typename T> struct LatArgs {
+  const void* in;        // complex (or real for R2C)
+  void* out;             // complex (or real for INV_REAL)
+  int B, L, logL, M;     // data viewed as [B][L][M], transform along L
+  int TZ, logTZ;         // columns per block
+  const cplx<T>* tw;     // twiddles of length L
+  T norm;                // 1/sqrt(L)
+  // LAT_MID
+  const T* s_d;          // [B][L][M] real
+  // LAT_UPDATE
+  const cplx<T>* z1;     // z^{k-1}
+  const cplx<T>* z2;     // z^{k-2}
+  cplx<T>* zout;         // z^k (may alias z2)
+  const T* w;            // [nz] weights or null
+  int nz;
+  T inv_L, lam_over_L, mu_prev, mu;
+  double* partial;       // [gridDim.x*gridDim.y][3] norm partials, or null
+  int* flag;             // non-finite flag
+};
+
+template <typename T> struct AxArgs {
+  const cplx<T>* in;
+  cplx<T>* out;
+  StoltConst sc;
+  Tables<T> tab;
+};
+
+// launchers (return cudaGetLastError())
+template <typename T> cudaError_t launch_lat(int mode, const LatArgs<T>& a, cudaStream_t s);
+template <typename T> cudaError_t launch_ax_fwd(const AxArgs<T>& a, int ncols, cudaStream_t s);
+template <typename T> cudaError_t launch_ax_adj(const AxArgs<T>& a, int ncols, cudaStream_t s);
+
+// FP64 min-max table (device), written as T
+template <typename T> cudaError_t build_minmax_table(int nz, int K, int J, T* out, cudaStream_t s);
+
+// reductions / elementwise
+template <typename T> cudaError_t launch_max_abs(const cplx<T>* x, size_t n, double* partial,
+                                                  int nblocks, double* out, cudaStream_t s);
+template <typename T> cudaError_t launch_norm2(const cplx<T>* x, size_t n, double* partial,
+                                                int nblocks, double* out, cudaStream_t s);
+cudaError_t launch_sum3(const double* partial, int n, double* out, cudaStream_t s);
+template <typename T> cudaError_t launch_scale(cplx<T>* x, size_t n, const double* denom,
+                                                cudaStream_t s);
+template <typename T> cudaError_t launch_extrapolate(const cplx<T>* z1, const cplx<T>* z2, T mu,
+                                                     cplx<T>* out, size_t n, cudaStream_t s);
+template <typename Tsrc, typename Tdst> cudaError_t launch_convert(const cplx<Tsrc>* x,
+                                                                   cplx<Tdst>* y, size_t n,
+                                                                   cudaStream_t s);
+template <typename T> cudaError_t launch_fill_start(cplx<T>* x, size_t n, cudaStream_t s);
+
+template <typename T> cudaError_t launch_rsub(const T* a, const T* b, T* y, size_t n,
+                                               cudaStream_t s);
+template <typename T> cudaError_t launch_caxpy(const cplx<T>* x, const cplx<T>* v, T alpha,
+                                                cplx<T>* y, size_t n, cudaStream_t s);
+
+int lat_tile(int L, int M);   // columns per block of a lateral pass
+
+}  // namespace isam

@@ -1,0 +1,758 @@
+// C ABI of the library: plans, forward/adjoint operators and the MBIR solve.
+//
+// Per application of A (B-scan, ny = 1) three kernels run:
+//   lateral FFT (x) -> k_ax_fwd (Stolt NUFFT + phases) -> lateral IFFT + Re;
+// per application of A^H:
+//   lateral FFT of the real spectra -> k_ax_adj -> lateral IFFT;
+// per FISTA iteration (Alg. 1) four:
+//   k_ax_fwd -> LAT_MID (IFFT, Re, - s_d, FFT) -> k_ax_adj -> LAT_UPDATE.
+// Volumes (ny > 1) add separate x passes around the y-axis fused passes.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "isam.h"
+#include "internal.cuh"
+
+using namespace isam;
+
+namespace {
+
+template <typename T> struct Impl {
+  Tables<T> tab{};
+  cplx<T>* eta_hat = nullptr;   // [ny][nx][nz]  lateral spectrum of the image
+  cplx<T>* spec = nullptr;      // [ny][nx][nk]  complex spectra (S, then R_hat)
+  cplx<T>* grad = nullptr;      // [ny][nx][nz]  G_hat / image temporaries
+  cplx<T>* zA = nullptr;        // solver iterates
+  cplx<T>* zB = nullptr;
+  T* s_tmp = nullptr;           // [ny][nx][nk]  real spectra temporary
+  T* s_host_stage = nullptr;    // device copy of host s_d for isam_solve_host
+  cplx<T>* out_stage = nullptr; // device image for isam_solve_host
+  bool ready = false;
+};
+
+}  // namespace
+
+struct isam_plan {
+  isam_params p{};
+  int nx = 0, ny = 0, nk = 0, nz = 0, K = 0, J = 6;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  StoltConst sc{};
+  Impl<float> f32;
+  Impl<double> f64;
+  double* partial = nullptr;    // reduction partials
+  int n_partial = 0;
+  double* dscal = nullptr;      // device scalars [8]
+  double* hscal = nullptr;      // pinned host mirror [8]
+  int* flag = nullptr;          // device non-finite flag
+  double L_cache = 0.0;
+  int64_t launches = 0;
+  size_t n_img = 0, n_spec = 0;
+  // opt-in per-kernel-class timing with CUDA events on the plan's stream
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<cudaEvent_t> ev_pending;   // start, stop pairs
+  std::vector<int> ev_class;
+  double prof_ms[ISAM_KCLASS_COUNT] = {0};
+  int64_t prof_n[ISAM_KCLASS_COUNT] = {0};
+};
+
+namespace {
+
+constexpr int RED_BLOCKS = 1024;
+// power iteration used when the caller gives no L: the top eigenvalues of
+// A^H A lie close together, so convergence takes hundreds of steps
+constexpr int kPowerIters = 1000;
+constexpr double kPowerRtol = 1e-11;
+
+isam_status from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return ISAM_OK;
+  if (e == cudaErrorMemoryAllocation) return ISAM_ERR_OOM;
+  return ISAM_ERR_CUDA;
+}
+
+cudaEvent_t take_event(isam_plan* P) {
+  cudaEvent_t e = nullptr;
+  if (!P->ev_pool.empty()) {
+    e = P->ev_pool.back();
+    P->ev_pool.pop_back();
+  } else if (cudaEventCreate(&e) != cudaSuccess) {
+    e = nullptr;
+  }
+  return e;
+}
+
+// Accumulate the elapsed times of recorded launches (call after a stream sync).
+void harvest_events(isam_plan* P) {
+  for (size_t i = 0; i + 1 < P->ev_pending.size(); i += 2) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, P->ev_pending[i], P->ev_pending[i + 1]) == cudaSuccess) {
+      P->prof_ms[P->ev_class[i / 2]] += ms;
+      P->prof_n[P->ev_class[i / 2]] += 1;
+    }
+    P->ev_pool.push_back(P->ev_pending[i]);
+    P->ev_pool.push_back(P->ev_pending[i + 1]);
+  }
+  P->ev_pending.clear();
+  P->ev_class.clear();
+}
+
+// Count (and, when profiling, time) one kernel launch of class `cls`.
+template <typename F> isam_status launch(isam_plan* P, int cls, F&& f) {
+  P->launches += 1;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (P->prof) {
+    e0 = take_event(P);
+    e1 = take_event(P);
+    if (e0 && e1) cudaEventRecord(e0, P->stream);
+  }
+  cudaError_t err = f();
+  if (P->prof && e0 && e1) {
+    cudaEventRecord(e1, P->stream);
+    P->ev_pending.push_back(e0);
+    P->ev_pending.push_back(e1);
+    P->ev_class.push_back(cls);
+  }
+  return from_cuda(err);
+}
+
+#define ISAM_TRY(expr)                              \
+  do {                                              \
+    isam_status _st = (expr);                       \
+    if (_st != ISAM_OK) return _st;                 \
+  } while (0)
+#define CUDA_TRY(expr) ISAM_TRY(from_cuda(expr))
+
+bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+int ilog2(int v) { int r = 0; while ((1 << r) < v) ++r; return r; }
+
+template <typename T> isam_status dalloc(T** p, size_t n) {
+  *p = nullptr;
+  if (n == 0) return ISAM_OK;
+  return from_cuda(cudaMalloc(reinterpret_cast<void**>(p), n * sizeof(T)));
+}
+
+template <typename T> void impl_free(Impl<T>& im) {
+  cudaFree(im.tab.tw_x); cudaFree(im.tab.tw_y); cudaFree(im.tab.tw_K);
+  cudaFree(im.tab.scale); cudaFree(im.tab.disp); cudaFree(im.tab.coef);
+  cudaFree(im.eta_hat); cudaFree(im.spec); cudaFree(im.grad);
+  cudaFree(im.zA); cudaFree(im.zB); cudaFree(im.s_tmp);
+  cudaFree(im.s_host_stage); cudaFree(im.out_stage);
+  im = Impl<T>();
+}
+
+// e^{-2 pi i m / L}, m < L, computed in FP64 then rounded to T
+template <typename T> isam_status upload_twiddles(cplx<T>** dst, int L) {
+  std::vector<cplx<T>> h(L);
+  for (int m = 0; m < L; ++m) {
+    const double a = -2.0 * M_PI * double(m) / double(L);
+    h[m] = mk<T>(T(cos(a)), T(sin(a)));
+  }
+  ISAM_TRY(dalloc(dst, L));
+  return from_cuda(cudaMemcpy(*dst, h.data(), sizeof(cplx<T>) * L, cudaMemcpyHostToDevice));
+}
+
+double host_kb_scale(int n, int K, int J) {
+  const double alpha = 2.34 * J;
+  const double v = double(n) / double(K);
+  const double r = sqrt(alpha * alpha - (M_PI * J * v) * (M_PI * J * v));
+  return (sinh(alpha) / alpha) / (sinh(r) / r);
+}
+
+template <typename T> size_t ax_adj_smem(int K, int J) {
+  return size_t(K) * 2 * sizeof(cplx<T>) + size_t(TABLE_D + 1) * 2 * J * sizeof(T);
+}
+
+template <typename T> bool precision_fits(const isam_plan* P) {
+  return ax_adj_smem<T>(P->K, P->J) <= 227u * 1024u;
+}
+
+template <typename T> isam_status impl_init(isam_plan* P, Impl<T>& im) {
+  if (im.ready) return ISAM_OK;
+  if (!precision_fits<T>(P)) return ISAM_ERR_UNSUPPORTED;
+  const isam_params& p = P->p;
+  ISAM_TRY(upload_twiddles<T>(&im.tab.tw_x, P->nx));
+  ISAM_TRY(upload_twiddles<T>(&im.tab.tw_y, P->ny));
+  ISAM_TRY(upload_twiddles<T>(&im.tab.tw_K, P->K));
+  // scaling s(n - nz/2) / sqrt(nz)
+  {
+    std::vector<T> h(P->nz);
+    for (int n = 0; n < P->nz; ++n)
+      h[n] = T(host_kb_scale(n - P->nz / 2, P->K, P->J) / sqrt(double(P->nz)));
+    ISAM_TRY(dalloc(&im.tab.scale, P->nz));
+    CUDA_TRY(cudaMemcpy(im.tab.scale, h.data(), sizeof(T) * P->nz, cudaMemcpyHostToDevice));
+  }
+  // dispersion phase e^{j phi(k_j)}, phi = sum a_i (k - k0)^i  (Eq. 7)
+  {
+    std::vector<cplx<T>> h(P->nk);
+    const double dk = (p.k_max - p.k_min) / (P->nk - 1);
+    const double k0 = 0.5 * (p.k_min + p.k_max);
+    for (int j = 0; j < P->nk; ++j) {
+      const double d = (p.k_min + dk * j) - k0;
+      double phi = 0.0, pw = 1.0;
+      for (int i = 0; i < p.n_disp; ++i) { pw *= d; phi += p.disp[i] * pw; }
+      h[j] = mk<T>(T(cos(phi)), T(sin(phi)));
+    }
+    ISAM_TRY(dalloc(&im.tab.disp, P->nk));
+    CUDA_TRY(cudaMemcpy(im.tab.disp, h.data(), sizeof(cplx<T>) * P->nk, cudaMemcpyHostToDevice));
+  }
+  ISAM_TRY(dalloc(&im.tab.coef, size_t(TABLE_D + 1) * 2 * P->J));
+  CUDA_TRY(build_minmax_table<T>(P->nz, P->K, P->J, im.tab.coef, P->stream));
+  ISAM_TRY(dalloc(&im.eta_hat, P->n_img));
+  ISAM_TRY(dalloc(&im.spec, P->n_spec));
+  ISAM_TRY(dalloc(&im.grad, P->n_img));
+  CUDA_TRY(cudaStreamSynchronize(P->stream));
+  harvest_events(P);
+  im.ready = true;
+  return ISAM_OK;
+}
+
+template <typename T> Impl<T>& impl_of(isam_plan* P);
+template <> Impl<float>& impl_of<float>(isam_plan* P) { return P->f32; }
+template <> Impl<double>& impl_of<double>(isam_plan* P) { return P->f64; }
+
+// ----------------------------------------------------------------------------
+// launch helpers
+// ----------------------------------------------------------------------------
+template <typename T>
+LatArgs<T> lat_args(const Impl<T>& im, int B, int L, int M, const cplx<T>* tw, const void* in,
+                    void* out) {
+  LatArgs<T> a{};
+  a.in = in; a.out = out;
+  a.B = B; a.L = L; a.logL = ilog2(L); a.M = M;
+  a.TZ = lat_tile(L, M); a.logTZ = ilog2(a.TZ);
+  a.tw = tw;
+  a.norm = T(1.0 / sqrt(double(L)));
+  (void)im;
+  return a;
+}
+
+template <typename T> isam_status lat(isam_plan* P, int mode, const LatArgs<T>& a) {
+  const int cls = mode == LAT_MID ? ISAM_KCLASS_LAT_MID
+                : mode == LAT_UPDATE ? ISAM_KCLASS_LAT_UPDATE : ISAM_KCLASS_LAT_FFT;
+  return launch(P, cls, [&] { return launch_lat<T>(mode, a, P->stream); });
+}
+
+template <typename T> AxArgs<T> ax_args(isam_plan* P, const Impl<T>& im, const cplx<T>* in,
+                                       cplx<T>* out) {
+  AxArgs<T> a{};
+  a.in = in; a.out = out; a.sc = P->sc; a.tab = im.tab;
+  return a;
+}
+
+// F_lat x (image or spectra layout with inner width W), possibly real input
+template <typename T> isam_status lat_forward(isam_plan* P, Impl<T>& im, const void* in,
+                                              cplx<T>* out, int W, bool real_in) {
+  const int m0 = real_in ? LAT_R2C_FWD : LAT_C2C_FWD;
+  if (P->ny == 1) return lat<T>(P, m0, lat_args<T>(im, 1, P->nx, W, im.tab.tw_x, in, out));
+  ISAM_TRY(lat<T>(P, m0, lat_args<T>(im, P->ny, P->nx, W, im.tab.tw_x, in, out)));
+  return lat<T>(P, LAT_C2C_FWD, lat_args<T>(im, 1, P->ny, P->nx * W, im.tab.tw_y, out, out));
+}
+
+// F_lat^{-1} x, complex or real (Re) output; `in` is overwritten for volumes
+template <typename T> isam_status lat_inverse(isam_plan* P, Impl<T>& im, cplx<T>* in, void* out,
+                                              int W, bool real_out) {
+  const int m1 = real_out ? LAT_INV_REAL : LAT_C2C_INV;
+  if (P->ny == 1) return lat<T>(P, m1, lat_args<T>(im, 1, P->nx, W, im.tab.tw_x, in, out));
+  ISAM_TRY(lat<T>(P, LAT_C2C_INV, lat_args<T>(im, 1, P->ny, P->nx * W, im.tab.tw_y, in, in)));
+  return lat<T>(P, m1, lat_args<T>(im, P->ny, P->nx, W, im.tab.tw_x, in, out));
+}
+
+template <typename T> isam_status op_forward(isam_plan* P, const void* eta, void* s) {
+  Impl<T>& im = impl_of<T>(P);
+  ISAM_TRY(lat_forward<T>(P, im, eta, im.eta_hat, P->nz, false));
+  ISAM_TRY(launch(P, ISAM_KCLASS_AX_FWD, [&] {
+    return launch_ax_fwd<T>(ax_args<T>(P, im, im.eta_hat, im.spec), P->nx * P->ny, P->stream);
+  }));
+  return lat_inverse<T>(P, im, im.spec, s, P->nk, true);
+}
+
+template <typename T> isam_status op_adjoint(isam_plan* P, const void* s, void* eta) {
+  Impl<T>& im = impl_of<T>(P);
+  ISAM_TRY(lat_forward<T>(P, im, s, im.spec, P->nk, true));
+  ISAM_TRY(launch(P, ISAM_KCLASS_AX_ADJ, [&] {
+    return launch_ax_adj<T>(ax_args<T>(P, im, im.spec, im.grad), P->nx * P->ny, P->stream);
+  }));
+  return lat_inverse<T>(P, im, im.grad, eta, P->nz, false);
+}
+
+template <typename T> isam_status max_abs_dev(isam_plan* P, const cplx<T>* x, double* out_host) {
+  P->launches += 1;   // two kernels
+  ISAM_TRY(launch(P, ISAM_KCLASS_MISC, [&] {
+    return launch_max_abs<T>(x, P->n_img, P->partial, RED_BLOCKS, P->dscal, P->stream);
+  }));
+  CUDA_TRY(cudaMemcpyAsync(P->hscal, P->dscal, sizeof(double), cudaMemcpyDeviceToHost, P->stream));
+  CUDA_TRY(cudaStreamSynchronize(P->stream));
+  harvest_events(P);
+  *out_host = P->hscal[0];
+  return ISAM_OK;
+}
+
+// power iteration for ||A^H A|| in precision T
+template <typename T> isam_status power_iteration(isam_plan* P, int iters, double rtol,
+                                                  const void* v0, int v0_double, double* L_out) {
+  Impl<T>& im = impl_of<T>(P);
+  ISAM_TRY(impl_init<T>(P, im));
+  if (!im.zA) ISAM_TRY(dalloc(&im.zA, P->n_img));
+  if (!im.zB) ISAM_TRY(dalloc(&im.zB, P->n_img));
+  if (!im.s_tmp) ISAM_TRY(dalloc(&im.s_tmp, P->n_spec));
+  cudaStream_t s = P->stream;
+  if (v0) {
+    const bool same = (sizeof(T) == 8) == (v0_double != 0);
+    if (same) {
+      CUDA_TRY(cudaMemcpyAsync(im.zA, v0, sizeof(cplx<T>) * P->n_img, cudaMemcpyDeviceToDevice, s));
+    } else if (sizeof(T) == 8) {
+      CUDA_TRY((launch_convert<float, double>(static_cast<const float2*>(v0),
+                                              reinterpret_cast<double2*>(im.zA), P->n_img, s)));
+    } else {
+      CUDA_TRY((launch_convert<double, float>(static_cast<const double2*>(v0),
+                                              reinterpret_cast<float2*>(im.zA), P->n_img, s)));
+    }
+  } else {
+    CUDA_TRY(launch_fill_start<T>(im.zA, P->n_img, s));
+  }
+  P->launches += 4;
+  CUDA_TRY(launch_norm2<T>(im.zA, P->n_img, P->partial, RED_BLOCKS, P->dscal, s));
+  CUDA_TRY(launch_scale<T>(im.zA, P->n_img, P->dscal, s));
+  double L = 0.0, L_prev = 0.0;
+  for (int it = 0; it < iters; ++it) {
+    ISAM_TRY(op_forward<T>(P, im.zA, im.s_tmp));
+    ISAM_TRY(op_adjoint<T>(P, im.s_tmp, im.zB));
+    P->launches += 3;
+    CUDA_TRY(launch_norm2<T>(im.zB, P->n_img, P->partial, RED_BLOCKS, P->dscal, s));
+    CUDA_TRY(launch_scale<T>(im.zB, P->n_img, P->dscal, s));
+    CUDA_TRY(cudaMemcpyAsync(P->hscal, P->dscal, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    harvest_events(P);
+    L = P->hscal[0];
+    std::swap(im.zA, im.zB);
+    if (L == 0.0) break;
+    if (fabs(L - L_prev) <= rtol * L) break;
+    L_prev = L;
+  }
+  *L_out = L;
+  return ISAM_OK;
+}
+
+// ----------------------------------------------------------------------------
+// FISTA (Alg. 1)
+// ----------------------------------------------------------------------------
+template <typename T> isam_status fista_iteration(isam_plan* P, Impl<T>& im, const T* s_d,
+                                                  const cplx<T>* z1, const cplx<T>* z2,
+                                                  cplx<T>* zout, const T* w, double lam,
+                                                  double L, double mu_prev, double mu,
+                                                  bool norms) {
+  cudaStream_t s = P->stream;
+  ISAM_TRY(launch(P, ISAM_KCLASS_AX_FWD, [&] {
+    return launch_ax_fwd<T>(ax_args<T>(P, im, im.eta_hat, im.spec), P->nx * P->ny, s);
+  }));
+  if (P->ny == 1) {
+    LatArgs<T> a = lat_args<T>(im, 1, P->nx, P->nk, im.tab.tw_x, im.spec, im.spec);
+    a.s_d = s_d;
+    ISAM_TRY(lat<T>(P, LAT_MID, a));
+  } else {
+    ISAM_TRY(lat<T>(P, LAT_C2C_INV, lat_args<T>(im, P->ny, P->nx, P->nk, im.tab.tw_x, im.spec, im.spec)));
+    LatArgs<T> a = lat_args<T>(im, 1, P->ny, P->nx * P->nk, im.tab.tw_y, im.spec, im.spec);
+    a.s_d = s_d;
+    ISAM_TRY(lat<T>(P, LAT_MID, a));
+    ISAM_TRY(lat<T>(P, LAT_C2C_FWD, lat_args<T>(im, P->ny, P->nx, P->nk, im.tab.tw_x, im.spec, im.spec)));
+  }
+  ISAM_TRY(launch(P, ISAM_KCLASS_AX_ADJ, [&] {
+    return launch_ax_adj<T>(ax_args<T>(P, im, im.spec, im.grad), P->nx * P->ny, s);
+  }));
+  LatArgs<T> u;
+  if (P->ny == 1) {
+    u = lat_args<T>(im, 1, P->nx, P->nz, im.tab.tw_x, im.grad, im.eta_hat);
+  } else {
+    ISAM_TRY(lat<T>(P, LAT_C2C_INV, lat_args<T>(im, P->ny, P->nx, P->nz, im.tab.tw_x, im.grad, im.grad)));
+    u = lat_args<T>(im, 1, P->ny, P->nx * P->nz, im.tab.tw_y, im.grad, im.eta_hat);
+  }
+  u.z1 = z1; u.z2 = z2; u.zout = zout; u.w = w; u.nz = P->nz;
+  u.inv_L = T(1.0 / L); u.lam_over_L = T(lam / L); u.mu_prev = T(mu_prev); u.mu = T(mu);
+  u.partial = norms ? P->partial : nullptr;
+  u.flag = P->flag;
+  ISAM_TRY(lat<T>(P, LAT_UPDATE, u));
+  if (norms) {
+    const int nblk = (u.M / u.TZ) * u.B;
+    ISAM_TRY(launch(P, ISAM_KCLASS_MISC, [&] { return launch_sum3(P->partial, nblk, P->dscal + 1, s); }));
+  }
+  if (P->ny > 1)
+    ISAM_TRY(lat<T>(P, LAT_C2C_FWD, lat_args<T>(im, P->ny, P->nx, P->nz, im.tab.tw_x, im.eta_hat, im.eta_hat)));
+  return ISAM_OK;
+}
+
+// t^1 = 1, t^{k+1} = (1 + sqrt(1 + 4 (t^k)^2))/2; mu_k = (t^k - 1)/t^{k+1}
+void momentum(int kmax, std::vector<double>& mu) {
+  std::vector<double> t(kmax + 2);
+  t[1] = 1.0;
+  for (int k = 1; k <= kmax; ++k) t[k + 1] = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t[k] * t[k]));
+  mu.assign(kmax + 1, 0.0);
+  for (int k = 1; k <= kmax; ++k) mu[k] = (t[k] - 1.0) / t[k + 1];
+}
+
+template <typename T> isam_status solve_impl(isam_plan* P, const T* s_d, const isam_solve_opts* o,
+                                             cplx<T>* eta_out, isam_solve_state* state,
+                                             isam_solve_info* info) {
+  Impl<T>& im = impl_of<T>(P);
+  cudaStream_t s = P->stream;
+  if (!im.zA) ISAM_TRY(dalloc(&im.zA, P->n_img));
+  if (!im.zB) ISAM_TRY(dalloc(&im.zB, P->n_img));
+  int64_t launches0 = P->launches;
+  const bool resume = state && state->k > 0;
+  // lambda = c ||A^H s_d||_inf unless given
+  double lam = o->lambda_abs;
+  if (resume && state->lambda > 0) lam = state->lambda;
+  if (!(lam > 0)) {
+    ISAM_TRY(op_adjoint<T>(P, s_d, im.zA));
+    double m = 0.0;
+    ISAM_TRY(max_abs_dev<T>(P, im.zA, &m));
+    lam = o->lambda_rel * m;
+  }
+  double L = o->L;
+  if (resume && state->L > 0) L = state->L;
+  if (!(L > 0)) {
+    if (!(P->L_cache > 0)) {
+      double Lc = 0.0;
+      if (precision_fits<double>(P))
+        ISAM_TRY(power_iteration<double>(P, kPowerIters, kPowerRtol, nullptr, 0, &Lc));
+      else
+        ISAM_TRY(power_iteration<T>(P, kPowerIters, kPowerRtol, nullptr, 0, &Lc));
+      P->L_cache = Lc;
+    }
+    L = P->L_cache;
+  }
+  if (!(L > 0)) return ISAM_ERR_INVALID;
+  const int k0 = resume ? state->k : 0;
+  std::vector<double> mu;
+  momentum(k0 + o->max_iter + 1, mu);
+  cplx<T>* zP = im.zA;   // holds z^{k-1}
+  cplx<T>* zQ = im.zB;   // holds z^{k-2}, receives z^k
+  CUDA_TRY(cudaMemsetAsync(P->flag, 0, sizeof(int), s));
+  if (resume) {
+    CUDA_TRY(cudaMemcpyAsync(zP, state->z1, sizeof(cplx<T>) * P->n_img, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(zQ, state->z2, sizeof(cplx<T>) * P->n_img, cudaMemcpyDeviceToDevice, s));
+    ISAM_TRY(launch(P, ISAM_KCLASS_MISC, [&] {
+      return launch_extrapolate<T>(zP, zQ, T(mu[k0]), im.grad, P->n_img, s);
+    }));
+    ISAM_TRY(lat_forward<T>(P, im, im.grad, im.eta_hat, P->nz, false));
+  } else {
+    CUDA_TRY(cudaMemsetAsync(zP, 0, sizeof(cplx<T>) * P->n_img, s));
+    CUDA_TRY(cudaMemsetAsync(zQ, 0, sizeof(cplx<T>) * P->n_img, s));
+    CUDA_TRY(cudaMemsetAsync(im.eta_hat, 0, sizeof(cplx<T>) * P->n_img, s));
+  }
+  const bool check = o->tol > 0;
+  const int every = std::max(1, o->check_every);
+  const double eps = o->eps > 0 ? o->eps : 1e-30;
+  double rr = -1.0;
+  int done = 0;
+  for (int it = 1; it <= o->max_iter; ++it) {
+    const int k = k0 + it;
+    const bool norms = check && (it % every == 0 || it == o->max_iter);
+    ISAM_TRY(fista_iteration<T>(P, im, s_d, zP, zQ, zQ, static_cast<const T*>(o->w_dev), lam, L,
+                                mu[k - 1], mu[k], norms));
+    std::swap(zP, zQ);   // zP = z^k, zQ = z^{k-1}
+    done = it;
+    if (norms) {
+      CUDA_TRY(cudaMemcpyAsync(P->hscal + 1, P->dscal + 1, 3 * sizeof(double),
+                               cudaMemcpyDeviceToHost, s));
+      CUDA_TRY(cudaStreamSynchronize(s));
+    harvest_events(P);
+      const double a = sqrt(P->hscal[1]), g = sqrt(P->hscal[2]), b = sqrt(P->hscal[3]);
+      rr = a / (std::max(g, b) + eps);
+      if (rr < o->tol) break;
+    }
+  }
+  // result: z^K, optionally with the residual added back (Alg. 1, last step)
+  if (o->residual_addback) {
+    if (!im.s_tmp) ISAM_TRY(dalloc(&im.s_tmp, P->n_spec));
+    ISAM_TRY(op_forward<T>(P, zP, im.s_tmp));
+    ISAM_TRY(launch(P, ISAM_KCLASS_MISC, [&] {
+      return launch_rsub<T>(s_d, im.s_tmp, im.s_tmp, P->n_spec, s);
+    }));
+    ISAM_TRY(op_adjoint<T>(P, im.s_tmp, im.grad));
+    ISAM_TRY(launch(P, ISAM_KCLASS_MISC, [&] {
+      return launch_caxpy<T>(zP, im.grad, T(1.0 / L), eta_out, P->n_img, s);
+    }));
+  } else if (zP != eta_out) {
+    CUDA_TRY(cudaMemcpyAsync(eta_out, zP, sizeof(cplx<T>) * P->n_img, cudaMemcpyDeviceToDevice, s));
+  }
+  if (state) {
+    CUDA_TRY(cudaMemcpyAsync(state->z1, zP, sizeof(cplx<T>) * P->n_img, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(state->z2, zQ, sizeof(cplx<T>) * P->n_img, cudaMemcpyDeviceToDevice, s));
+    state->k = k0 + done;
+    state->lambda = lam;
+    state->L = L;
+  }
+  int hflag = 0;
+  CUDA_TRY(cudaMemcpyAsync(P->hscal + 4, P->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+    harvest_events(P);
+  memcpy(&hflag, P->hscal + 4, sizeof(int));
+  isam_status st = hflag ? ISAM_ERR_NONFINITE : ISAM_OK;
+  if (info) {
+    info->iterations = done;
+    info->rr = rr;
+    info->lambda = lam;
+    info->L = L;
+    info->status = st;
+  }
+  (void)launches0;
+  return st;
+}
+
+isam_status validate(const isam_params* p) {
+  if (!p) return ISAM_ERR_INVALID;
+  const int nz = p->nz ? p->nz : p->nk;
+  if (!pow2(p->nx) || !pow2(p->ny) || !pow2(p->nk) || !pow2(nz)) return ISAM_ERR_INVALID;
+  if (p->nx > 4096 || p->ny > 4096) return ISAM_ERR_UNSUPPORTED;
+  if (p->nk < 16 || nz < 16) return ISAM_ERR_UNSUPPORTED;
+  if (nz < p->nk || nz > 2048) return ISAM_ERR_UNSUPPORTED;
+  if (!(p->k_min > 0) || !(p->k_max > p->k_min)) return ISAM_ERR_INVALID;
+  if (p->nx > 1 && !(p->dx > 0)) return ISAM_ERR_INVALID;
+  if (p->ny > 1 && !(p->dy > 0)) return ISAM_ERR_INVALID;
+  if (p->n_disp < 0 || p->n_disp > 4) return ISAM_ERR_INVALID;
+  if (p->precision != ISAM_FP32 && p->precision != ISAM_FP64) return ISAM_ERR_INVALID;
+  const int J = p->nufft_J ? p->nufft_J : 6;
+  if (J != 4 && J != 6 && J != 8) return ISAM_ERR_UNSUPPORTED;
+  const int os = p->nufft_os ? p->nufft_os : 2;
+  if (os != 2) return ISAM_ERR_UNSUPPORTED;
+  if (!isfinite(p->z0)) return ISAM_ERR_INVALID;
+  for (int i = 0; i < 4; ++i)
+    if (!isfinite(p->disp[i])) return ISAM_ERR_INVALID;
+  return ISAM_OK;
+}
+
+void split_ff(double v, float* hi, float* lo) {
+  *hi = float(v);
+  *lo = float(v - double(*hi));
+}
+
+void make_stolt(isam_plan* P) {
+  const isam_params& p = P->p;
+  StoltConst& c = P->sc;
+  const double dk = (p.k_max - p.k_min) / (P->nk - 1);
+  c.kap = p.k_min / dk;
+  c.Qx = P->nx > 1 ? pow(2.0 * M_PI / (P->nx * p.dx * dk), 2.0) : 0.0;
+  c.Qy = P->ny > 1 ? pow(2.0 * M_PI / (P->ny * p.dy * dk), 2.0) : 0.0;
+  c.zeta = dk * p.z0 / (2.0 * M_PI);
+  c.c0d = fmod(2.0 * c.kap, double(P->K));
+  c.I0 = int(floor(c.c0d));
+  c.f0 = float(c.c0d - double(c.I0));
+  split_ff(c.kap, &c.kap_hi, &c.kap_lo);
+  split_ff(c.Qx, &c.qx_hi, &c.qx_lo);
+  split_ff(c.Qy, &c.qy_hi, &c.qy_lo);
+  split_ff(c.zeta, &c.zeta_hi, &c.zeta_lo);
+  c.K = P->K; c.logK = ilog2(P->K);
+  c.nx = P->nx; c.ny = P->ny; c.nk = P->nk; c.nz = P->nz; c.J = P->J;
+  c.focus = p.z0 != 0.0;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() { if (prev >= 0) cudaSetDevice(prev); }
+};
+
+}  // namespace
+
+extern "C" {
+
+const char* isam_status_string(isam_status s) {
+  switch (s) {
+    case ISAM_OK: return "ok";
+    case ISAM_ERR_INVALID: return "invalid argument";
+    case ISAM_ERR_OOM: return "out of device memory";
+    case ISAM_ERR_CUDA: return "CUDA error";
+    case ISAM_ERR_NONFINITE: return "non-finite value in the solve";
+    case ISAM_ERR_TIMEOUT: return "device wait timed out";
+    case ISAM_ERR_UNSUPPORTED: return "unsupported size or option";
+  }
+  return "unknown status";
+}
+
+isam_status isam_plan_create(const isam_params* p, void* stream, isam_plan** out) {
+  if (!out) return ISAM_ERR_INVALID;
+  *out = nullptr;
+  ISAM_TRY(validate(p));
+  isam_plan* P = new (std::nothrow) isam_plan();
+  if (!P) return ISAM_ERR_OOM;
+  P->p = *p;
+  P->nx = p->nx; P->ny = p->ny; P->nk = p->nk; P->nz = p->nz ? p->nz : p->nk;
+  P->p.nz = P->nz;
+  P->K = 2 * P->nz;
+  P->J = p->nufft_J ? p->nufft_J : 6;
+  P->stream = static_cast<cudaStream_t>(stream);
+  P->n_img = size_t(P->nx) * P->ny * P->nz;
+  P->n_spec = size_t(P->nx) * P->ny * P->nk;
+  cudaGetDevice(&P->device);
+  make_stolt(P);
+  isam_status st = ISAM_OK;
+  {
+    // partial sums: reductions use RED_BLOCKS, the FISTA update one per block
+    const int L = P->ny == 1 ? P->nx : P->ny;
+    const int M = P->ny == 1 ? P->nz : P->nx * P->nz;
+    P->n_partial = std::max(RED_BLOCKS, M / lat_tile(L, M));
+  }
+  if (st == ISAM_OK) st = dalloc(&P->partial, size_t(P->n_partial) * 3);
+  if (st == ISAM_OK) st = dalloc(&P->dscal, 8);
+  if (st == ISAM_OK) st = dalloc(&P->flag, 1);
+  if (st == ISAM_OK) st = from_cuda(cudaMallocHost(reinterpret_cast<void**>(&P->hscal), 8 * sizeof(double)));
+  if (st == ISAM_OK) {
+    if (p->precision == ISAM_FP64) st = impl_init<double>(P, P->f64);
+    else st = impl_init<float>(P, P->f32);
+  }
+  if (st != ISAM_OK) {
+    isam_plan_destroy(P);
+    return st;
+  }
+  *out = P;
+  return ISAM_OK;
+}
+
+void isam_plan_destroy(isam_plan* P) {
+  if (!P) return;
+  DeviceGuard g(P->device);
+  if (P->stream) cudaStreamSynchronize(P->stream);
+  else cudaDeviceSynchronize();
+  impl_free(P->f32);
+  impl_free(P->f64);
+  cudaFree(P->partial);
+  cudaFree(P->dscal);
+  cudaFree(P->flag);
+  if (P->hscal) cudaFreeHost(P->hscal);
+  harvest_events(P);
+  for (cudaEvent_t e : P->ev_pool) cudaEventDestroy(e);
+  delete P;
+}
+
+isam_status isam_set_stream(isam_plan* P, void* stream) {
+  if (!P) return ISAM_ERR_INVALID;
+  P->stream = static_cast<cudaStream_t>(stream);
+  return ISAM_OK;
+}
+
+isam_status isam_forward(isam_plan* P, const void* eta, void* s) {
+  if (!P || !eta || !s) return ISAM_ERR_INVALID;
+  DeviceGuard g(P->device);
+  P->launches = 0;
+  if (P->p.precision == ISAM_FP64) return op_forward<double>(P, eta, s);
+  return op_forward<float>(P, eta, s);
+}
+
+isam_status isam_adjoint(isam_plan* P, const void* s, void* eta) {
+  if (!P || !eta || !s) return ISAM_ERR_INVALID;
+  DeviceGuard g(P->device);
+  P->launches = 0;
+  if (P->p.precision == ISAM_FP64) return op_adjoint<double>(P, s, eta);
+  return op_adjoint<float>(P, s, eta);
+}
+
+static isam_status check_opts(const isam_plan* P, const isam_solve_opts* o) {
+  if (!o) return ISAM_ERR_INVALID;
+  if (o->max_iter < 1) return ISAM_ERR_INVALID;
+  if (!(o->lambda_abs > 0) && !(o->lambda_rel >= 0)) return ISAM_ERR_INVALID;
+  if (o->tol < 0 || !isfinite(o->tol)) return ISAM_ERR_INVALID;
+  (void)P;
+  return ISAM_OK;
+}
+
+isam_status isam_solve(isam_plan* P, const void* s_d, const isam_solve_opts* o, void* eta_out,
+                       isam_solve_state* state, isam_solve_info* info) {
+  if (!P || !s_d || !eta_out) return ISAM_ERR_INVALID;
+  ISAM_TRY(check_opts(P, o));
+  if (state && (!state->z1 || !state->z2 || state->k < 0)) return ISAM_ERR_INVALID;
+  DeviceGuard g(P->device);
+  P->launches = 0;
+  if (P->p.precision == ISAM_FP64)
+    return solve_impl<double>(P, static_cast<const double*>(s_d), o, static_cast<double2*>(eta_out),
+                              state, info);
+  return solve_impl<float>(P, static_cast<const float*>(s_d), o, static_cast<float2*>(eta_out),
+                           state, info);
+}
+
+}  // extern "C"
+
+template <typename T>
+static isam_status solve_host_impl(isam_plan* P, const void* s_h, const isam_solve_opts* o,
+                                   void* eta_h, isam_solve_info* info) {
+  Impl<T>& im = impl_of<T>(P);
+  if (!im.s_host_stage) ISAM_TRY(dalloc(&im.s_host_stage, P->n_spec));
+  if (!im.out_stage) ISAM_TRY(dalloc(&im.out_stage, P->n_img));
+  CUDA_TRY(cudaMemcpyAsync(im.s_host_stage, s_h, sizeof(T) * P->n_spec, cudaMemcpyHostToDevice,
+                           P->stream));
+  ISAM_TRY(solve_impl<T>(P, im.s_host_stage, o, im.out_stage, nullptr, info));
+  CUDA_TRY(cudaMemcpyAsync(eta_h, im.out_stage, sizeof(cplx<T>) * P->n_img,
+                           cudaMemcpyDeviceToHost, P->stream));
+  return from_cuda(cudaStreamSynchronize(P->stream));
+}
+
+extern "C" {
+
+isam_status isam_solve_host(isam_plan* P, const void* s_h, const isam_solve_opts* o, void* eta_h,
+                            isam_solve_info* info) {
+  if (!P || !s_h || !eta_h) return ISAM_ERR_INVALID;
+  ISAM_TRY(check_opts(P, o));
+  DeviceGuard g(P->device);
+  P->launches = 0;
+  if (P->p.precision == ISAM_FP64) return solve_host_impl<double>(P, s_h, o, eta_h, info);
+  return solve_host_impl<float>(P, s_h, o, eta_h, info);
+}
+
+isam_status isam_lipschitz(isam_plan* P, int32_t iters, double rtol, const void* v0,
+                           double* L_out) {
+  if (!P || !L_out || iters < 1 || !(rtol >= 0)) return ISAM_ERR_INVALID;
+  DeviceGuard g(P->device);
+  P->launches = 0;
+  const int v0_double = P->p.precision == ISAM_FP64;
+  double L = 0.0;
+  if (precision_fits<double>(P))
+    ISAM_TRY(power_iteration<double>(P, iters, rtol, v0, v0_double, &L));
+  else if (P->p.precision == ISAM_FP64)
+    return ISAM_ERR_UNSUPPORTED;
+  else
+    ISAM_TRY(power_iteration<float>(P, iters, rtol, v0, v0_double, &L));
+  P->L_cache = L;
+  *L_out = L;
+  return ISAM_OK;
+}
+
+isam_status isam_max_abs(isam_plan* P, const void* eta, double* out) {
+  if (!P || !eta || !out) return ISAM_ERR_INVALID;
+  DeviceGuard g(P->device);
+  if (P->p.precision == ISAM_FP64) return max_abs_dev<double>(P, static_cast<const double2*>(eta), out);
+  return max_abs_dev<float>(P, static_cast<const float2*>(eta), out);
+}
+
+int64_t isam_last_launch_count(const isam_plan* P) { return P ? P->launches : -1; }
+
+isam_status isam_profile_enable(isam_plan* P, int32_t on) {
+  if (!P) return ISAM_ERR_INVALID;
+  DeviceGuard g(P->device);
+  CUDA_TRY(cudaStreamSynchronize(P->stream));
+  harvest_events(P);
+  P->prof = on != 0;
+  return ISAM_OK;
+}
+
+isam_status isam_profile_read(isam_plan* P, double* ms, int64_t* counts, int32_t reset) {
+  if (!P || !ms || !counts) return ISAM_ERR_INVALID;
+  DeviceGuard g(P->device);
+  CUDA_TRY(cudaStreamSynchronize(P->stream));
+  harvest_events(P);
+  for (int c = 0; c < ISAM_KCLASS_COUNT; ++c) {
+    ms[c] = P->prof_ms[c];
+    counts[c] = P->prof_n[c];
+    if (reset) { P->prof_ms[c] = 0.0; P->prof_n[c] = 0; }
+  }
+  return ISAM_OK;
+}
+
+}  // extern "C"

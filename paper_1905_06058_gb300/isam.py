@@ -1,0 +1,272 @@
+"""Thin ctypes binding over the C ABI of libisam.so (include/isam.h).
+
+Argument marshalling only: every step of the forward model, the adjoint and
+the solve runs in the library's CUDA kernels.  PyTorch provides device
+memory and the current CUDA stream.  There is no CPU fallback: if the shared
+library is missing or cannot be loaded, the import of this module fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libisam.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is not built; run `python __graft_entry__.py` (build())")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+ISAM_FP32, ISAM_FP64 = 0, 1
+STATUS = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "CUDA error",
+          4: "non-finite value in the solve", 5: "device wait timed out",
+          6: "unsupported size or option"}
+
+
+class IsamParams(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nk", ctypes.c_int32),
+                ("nz", ctypes.c_int32), ("k_min", ctypes.c_double), ("k_max", ctypes.c_double),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("na", ctypes.c_double),
+                ("z0", ctypes.c_double), ("n_disp", ctypes.c_int32),
+                ("disp", ctypes.c_double * 4), ("precision", ctypes.c_int32),
+                ("nufft_J", ctypes.c_int32), ("nufft_os", ctypes.c_int32)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("lambda_rel", ctypes.c_double), ("lambda_abs", ctypes.c_double),
+                ("max_iter", ctypes.c_int32), ("tol", ctypes.c_double),
+                ("check_every", ctypes.c_int32), ("w_dev", ctypes.c_void_p),
+                ("residual_addback", ctypes.c_int32), ("L", ctypes.c_double),
+                ("eps", ctypes.c_double)]
+
+
+class SolveState(ctypes.Structure):
+    _fields_ = [("z1", ctypes.c_void_p), ("z2", ctypes.c_void_p), ("k", ctypes.c_int32),
+                ("lambda_", ctypes.c_double), ("L", ctypes.c_double)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("rr", ctypes.c_double),
+                ("lambda_", ctypes.c_double), ("L", ctypes.c_double), ("status", ctypes.c_int32)]
+
+
+_P = ctypes.c_void_p
+_SIGS = {
+    "isam_plan_create": (ctypes.c_int, [ctypes.POINTER(IsamParams), _P, ctypes.POINTER(_P)]),
+    "isam_plan_destroy": (None, [_P]),
+    "isam_set_stream": (ctypes.c_int, [_P, _P]),
+    "isam_forward": (ctypes.c_int, [_P, _P, _P]),
+    "isam_adjoint": (ctypes.c_int, [_P, _P, _P]),
+    "isam_solve": (ctypes.c_int, [_P, _P, ctypes.POINTER(SolveOpts), _P,
+                                  ctypes.POINTER(SolveState), ctypes.POINTER(SolveInfo)]),
+    "isam_solve_host": (ctypes.c_int, [_P, _P, ctypes.POINTER(SolveOpts), _P,
+                                       ctypes.POINTER(SolveInfo)]),
+    "isam_lipschitz": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_double, _P,
+                                      ctypes.POINTER(ctypes.c_double)]),
+    "isam_max_abs": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_double)]),
+    "isam_last_launch_count": (ctypes.c_int64, [_P]),
+    "isam_profile_enable": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "isam_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]),
+    "isam_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+class IsamError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {STATUS.get(status, status)} (status {status})")
+        self.status = status
+
+
+def _check(st: int, where: str) -> None:
+    if st != 0:
+        raise IsamError(st, where)
+
+
+def lib() -> ctypes.CDLL:
+    return _lib
+
+
+def make_params(geom, precision: str = "fp32", J: int = 6) -> IsamParams:
+    p = IsamParams()
+    p.nx, p.ny, p.nk, p.nz = int(geom.nx), int(geom.ny), int(geom.nk), int(geom.nz or geom.nk)
+    p.k_min, p.k_max = float(geom.k_min), float(geom.k_max)
+    p.dx, p.dy = float(geom.dx), float(geom.dy)
+    p.na, p.z0 = float(geom.na), float(geom.z0)
+    disp = list(geom.disp) + [0.0] * (4 - len(geom.disp))
+    p.n_disp = 4
+    for i in range(4):
+        p.disp[i] = float(disp[i])
+    p.precision = ISAM_FP64 if precision == "fp64" else ISAM_FP32
+    p.nufft_J = int(J)
+    p.nufft_os = 2
+    return p
+
+
+def _stream_handle(stream) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+class Plan:
+    """A plan for one geometry: isam_plan_create / isam_forward / isam_adjoint / isam_solve."""
+
+    def __init__(self, geom, precision: str = "fp32", J: int = 6, stream=None):
+        import torch
+        self.geom = geom
+        self.precision = precision
+        self.real_dtype = torch.float64 if precision == "fp64" else torch.float32
+        self.cplx_dtype = torch.complex128 if precision == "fp64" else torch.complex64
+        self.image_shape = (geom.ny, geom.nx, geom.nz or geom.nk)
+        self.spec_shape = (geom.ny, geom.nx, geom.nk)
+        self._params = make_params(geom, precision, J)
+        h = _P()
+        _check(_lib.isam_plan_create(ctypes.byref(self._params), _P(_stream_handle(stream)),
+                                     ctypes.byref(h)), "isam_plan_create")
+        self._h = h
+
+    # -- helpers -----------------------------------------------------------------
+    def _dev(self, t, dtype, shape, name):
+        import torch
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise TypeError(f"{name} must be a CUDA tensor")
+        if t.dtype != dtype or tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+            raise ValueError(f"{name}: need contiguous {dtype} {shape}, got {t.dtype} "
+                             f"{tuple(t.shape)}")
+        return _P(t.data_ptr())
+
+    def _sync_stream(self):
+        _check(_lib.isam_set_stream(self._h, _P(_stream_handle(None))), "isam_set_stream")
+
+    @property
+    def handle(self):
+        return self._h
+
+    def last_launch_count(self) -> int:
+        return int(_lib.isam_last_launch_count(self._h))
+
+    KERNEL_CLASSES = ("ax_fwd", "ax_adj", "lat_mid", "lat_update", "lat_fft", "misc")
+
+    def profile(self, on: bool) -> None:
+        """Time every kernel launch of this plan with CUDA events (per class)."""
+        self._sync_stream()
+        _check(_lib.isam_profile_enable(self._h, int(bool(on))), "isam_profile_enable")
+
+    def profile_read(self, reset: bool = True) -> dict:
+        n = len(self.KERNEL_CLASSES)
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_int64 * n)()
+        _check(_lib.isam_profile_read(self._h, ms, cnt, int(bool(reset))), "isam_profile_read")
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(self.KERNEL_CLASSES)}
+
+    # -- operators ---------------------------------------------------------------
+    def forward(self, eta, out=None):
+        """s = A eta (real spectra)."""
+        import torch
+        self._sync_stream()
+        if out is None:
+            out = torch.empty(self.spec_shape, dtype=self.real_dtype, device=eta.device)
+        _check(_lib.isam_forward(self._h, self._dev(eta, self.cplx_dtype, self.image_shape, "eta"),
+                                 self._dev(out, self.real_dtype, self.spec_shape, "out")),
+               "isam_forward")
+        return out
+
+    def adjoint(self, s, out=None):
+        """eta = A^H s."""
+        import torch
+        self._sync_stream()
+        if out is None:
+            out = torch.empty(self.image_shape, dtype=self.cplx_dtype, device=s.device)
+        _check(_lib.isam_adjoint(self._h, self._dev(s, self.real_dtype, self.spec_shape, "s"),
+                                 self._dev(out, self.cplx_dtype, self.image_shape, "out")),
+               "isam_adjoint")
+        return out
+
+    def _opts(self, lambda_rel, lambda_abs, max_iter, tol, check_every, w, addback, L, eps):
+        o = SolveOpts()
+        o.lambda_rel, o.lambda_abs = float(lambda_rel), float(lambda_abs)
+        o.max_iter, o.tol, o.check_every = int(max_iter), float(tol), int(check_every)
+        o.w_dev = None if w is None else self._dev(w, self.real_dtype, (self.image_shape[2],), "w")
+        o.residual_addback = int(bool(addback))
+        o.L, o.eps = float(L), float(eps)
+        return o
+
+    def solve(self, s, lambda_rel=0.01, lambda_abs=0.0, max_iter=100, tol=0.0, check_every=10,
+              w=None, addback=False, L=0.0, eps=0.0, out=None, state: Optional[dict] = None):
+        """MBIR solve (Alg. 1).  Returns (eta, info dict).  ``state`` (optional) is a dict
+        with CUDA tensors 'z1', 'z2' (images) and ints/floats 'k', 'lambda', 'L'; it is
+        updated in place for checkpoint / resume."""
+        import torch
+        self._sync_stream()
+        if out is None:
+            out = torch.empty(self.image_shape, dtype=self.cplx_dtype, device=s.device)
+        o = self._opts(lambda_rel, lambda_abs, max_iter, tol, check_every, w, addback, L, eps)
+        info = SolveInfo()
+        st_ptr = None
+        if state is not None:
+            st = SolveState()
+            st.z1 = self._dev(state["z1"], self.cplx_dtype, self.image_shape, "state.z1")
+            st.z2 = self._dev(state["z2"], self.cplx_dtype, self.image_shape, "state.z2")
+            st.k = int(state.get("k", 0))
+            st.lambda_ = float(state.get("lambda", 0.0))
+            st.L = float(state.get("L", 0.0))
+            st_ptr = ctypes.byref(st)
+        _check(_lib.isam_solve(self._h, self._dev(s, self.real_dtype, self.spec_shape, "s"),
+                               ctypes.byref(o), self._dev(out, self.cplx_dtype, self.image_shape,
+                                                          "out"), st_ptr, ctypes.byref(info)),
+               "isam_solve")
+        if state is not None:
+            state["k"], state["lambda"], state["L"] = st.k, st.lambda_, st.L
+        return out, dict(iterations=info.iterations, rr=info.rr, lam=info.lambda_, L=info.L,
+                         status=info.status)
+
+    def solve_host(self, s_host, out_host, lambda_rel=0.01, lambda_abs=0.0, max_iter=100,
+                   tol=0.0, check_every=10, L=0.0, eps=0.0, addback=False):
+        """Solve with host buffers (CPU tensors, ideally pinned): copies in and out."""
+        self._sync_stream()
+        o = self._opts(lambda_rel, lambda_abs, max_iter, tol, check_every, None, addback, L, eps)
+        info = SolveInfo()
+        for t, dt, shp, nm in ((s_host, self.real_dtype, self.spec_shape, "s_host"),
+                               (out_host, self.cplx_dtype, self.image_shape, "out_host")):
+            if t.is_cuda or t.dtype != dt or tuple(t.shape) != shp or not t.is_contiguous():
+                raise ValueError(f"{nm}: need contiguous host {dt} {shp}")
+        _check(_lib.isam_solve_host(self._h, _P(s_host.data_ptr()), ctypes.byref(o),
+                                    _P(out_host.data_ptr()), ctypes.byref(info)),
+               "isam_solve_host")
+        return dict(iterations=info.iterations, rr=info.rr, lam=info.lambda_, L=info.L,
+                    status=info.status)
+
+    def lipschitz(self, iters=100, rtol=1e-9, v0=None) -> float:
+        self._sync_stream()
+        L = ctypes.c_double()
+        p = None if v0 is None else self._dev(v0, self.cplx_dtype, self.image_shape, "v0")
+        _check(_lib.isam_lipschitz(self._h, int(iters), float(rtol), p, ctypes.byref(L)),
+               "isam_lipschitz")
+        return L.value
+
+    def max_abs(self, eta) -> float:
+        self._sync_stream()
+        v = ctypes.c_double()
+        _check(_lib.isam_max_abs(self._h, self._dev(eta, self.cplx_dtype, self.image_shape, "eta"),
+                                 ctypes.byref(v)), "isam_max_abs")
+        return v.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.isam_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
