@@ -1,0 +1,400 @@
+#!/usr/bin/env python
+"""Benchmark of the MBIR full-range ISAM solve (Alg. 1) on GB300.
+
+Workload (N = 1): the 1024 A-scan x 2048 spectral-sample B-scan, layered
+tissue-like specimen, 12-bit counts with background subtraction, FP32; one
+step = one MBIR solve of `--iters` (200) FISTA iterations including lambda =
+0.01 ||A^H s_d||_inf and the relative-residual evaluation every 20 iterations.
+The Lipschitz constant is a per-geometry constant cached in the plan (first
+warm-up step).  value = FISTA iterations per second over all ranks; ranks
+solve independent B-scans (replicas, weak scaling, no data-path collective).
+
+Prints one JSON line.  `--impl reference` times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FISTA iters/s (A+Aᴴ) at 1024×2048 B-scan & 256²×2048 vol; % HBM roofline"
+UNIT = "iter/s"
+CHECK_EVERY = 20
+L2_FLUSH_BYTES = 256 << 20     # > 129 MB L2
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--iters", type=int, default=200)
+    ap.add_argument("--no-extras", action="store_true", help="skip A+A^H, FP64 and volume lines")
+    ap.add_argument("--volume", action="store_true", help="also time the 256^2 x 2048 volume")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--L", type=float, default=0.0,
+                    help="Lipschitz constant to use (0: power-iteration estimate, cached)")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ----------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ----------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle timing (the reported baseline and the reference arm)
+# ----------------------------------------------------------------------------
+def oracle_iteration_rate(seconds: float, nx_slice: int = 64):
+    """FP64 oracle FISTA iterations on a slice of the workload (same band,
+    spectral and depth sampling, dispersion; `nx_slice` of the 1024 A-scans),
+    timed after one warm iteration; the per-iteration time is scaled by
+    1024 / nx_slice (cost is linear in the number of A-scans)."""
+    from oracle import isam_oracle as O
+    from paper_1905_06058_gb300 import inputs as I
+    wl = I.config2(dtype=np.complex64)
+    g = wl.geom
+    g.nx = nx_slice
+    eta = wl.eta[:, :nx_slice].astype(np.complex128)
+    op = O.IsamOracle(g, "nufft")
+    s = op.forward(eta)
+    lam = 0.01 * np.abs(op.adjoint(s)).max()
+    L = 1.4
+    O.fista(op.forward, op.adjoint, s, lam, L, max_iter=1, shape=op.image_shape)   # warm
+    n, t0 = 0, time.perf_counter()
+    while True:
+        O.fista(op.forward, op.adjoint, s, lam, L, max_iter=1, shape=op.image_shape)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= seconds and n >= 2:
+            break
+    per_iter_full = el / n * (1024 / nx_slice)
+    return 1.0 / per_iter_full, n, el, nx_slice
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    per_step = max(args.cpu_seconds / max(args.steps, 1), 0.5)
+    t0 = time.perf_counter()
+    rate, n, el, nxs = oracle_iteration_rate(per_step * args.steps)
+    sample = (f"FP64 NumPy oracle (nufft mode, J=6) FISTA iterations on a {nxs}-A-scan slice of "
+              f"the 1024x2048 B-scan ({n} iterations, {el:.1f} s), scaled x{1024 // nxs}")
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 / rate * args.iters, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "bscan_1024x2048_fp32", "nx": 1024, "nk": 2048, "nz": 2048,
+                       "iters_per_step": args.iters},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "wall_s": time.perf_counter() - t0}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+def algorithmic_bytes(cls: str, n_img: int, n_spec: int, real_bytes=4) -> int:
+    """Compulsory HBM bytes per launch of each kernel class (B-scan layout)."""
+    c = 2 * real_bytes
+    return {"ax_fwd": c * (n_img + n_spec),          # read eta_hat, write S
+            "ax_adj": c * (n_spec + n_img),          # read R_hat, write G_hat
+            "lat_mid": c * n_spec * 2 + real_bytes * n_spec,   # S, s_d in; R_hat out
+            "lat_update": c * n_img * 5}.get(cls)    # G, z1, z2 in; z, eta_hat out
+
+
+# DRAM bytes per launch from ncu captures of the current kernels (profiles/);
+# None where no capture of the current kernel exists.
+NCU_TRAFFIC = {}
+
+
+def make_problem(torch, plan, wl, seed):
+    from paper_1905_06058_gb300 import inputs as I
+    eta = torch.from_numpy(wl.eta.astype(np.complex64)).cuda()
+    s_clean = plan.forward(eta).cpu().numpy()
+    k = wl.geom.k_min + (wl.geom.k_max - wl.geom.k_min) / (wl.geom.nk - 1) * np.arange(wl.geom.nk)
+    s = I.detector_counts(s_clean, k, np.random.default_rng(seed))
+    return torch.from_numpy(s).cuda(), eta
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    import __graft_entry__ as G
+    if rank == 0:
+        G.build()
+    if world > 1:
+        torch.distributed.barrier()
+    G.build()
+    from paper_1905_06058_gb300 import inputs as I
+    from paper_1905_06058_gb300.isam import Plan
+
+    wl = I.config2(dtype=np.complex64)
+    if rank:
+        wl.eta = I.layered_specimen(np.random.default_rng(wl.seed + 7919 * rank), wl.eta.shape,
+                                    6, 0.02, 200, np.complex64)
+    g = wl.geom
+    plan = Plan(g, precision="fp32")
+    s_d, _ = make_problem(torch, plan, wl, wl.seed + rank)
+    out = torch.empty(plan.image_shape, dtype=torch.complex64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    opts = dict(lambda_rel=wl.lambda_rel, max_iter=args.iters, tol=1e-12, check_every=CHECK_EVERY,
+                L=args.L)
+
+    for _ in range(args.warmup):
+        plan.solve(s_d, out=out, **opts)
+    torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    plan.profile(True)
+    clocks = Clocks(local)
+    launches = 0
+    iters_done = 0
+    infos = []
+    for i in range(args.steps):
+        flush.zero_()                           # evict L2 between timed steps
+        ev[i][0].record(stream)
+        _, info = plan.solve(s_d, out=out, **opts)
+        ev[i][1].record(stream)
+        launches += plan.last_launch_count()
+        iters_done += info["iterations"]
+        infos.append(info)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    prof = plan.profile_read()
+    plan.profile(False)
+    total_ms = sum(a.elapsed_time(b) for a, b in ev)
+    if world > 1:
+        t = torch.tensor([total_ms, iters_done], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        torch.distributed.all_reduce(tmax[:1], op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(t[1:], op=torch.distributed.ReduceOp.SUM)
+        total_ms, all_iters = float(tmax[0]), float(t[1])
+        torch.distributed.barrier()
+    else:
+        all_iters = iters_done
+    value = all_iters / (total_ms / 1000.0)
+
+    # dominant kernel and its live roofline
+    n_img, n_spec = plan.image_shape[1] * plan.image_shape[2], plan.spec_shape[1] * plan.spec_shape[2]
+    kern = {k: {"ms": v[0], "launches": v[1], "share": None} for k, v in prof.items()}
+    tot = sum(v["ms"] for v in kern.values()) or 1.0
+    for v in kern.values():
+        v["share"] = v["ms"] / tot
+    dom = max((k for k in kern if algorithmic_bytes(k, n_img, n_spec)), key=lambda k: kern[k]["ms"])
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = peaks.get("hbm_gbs", 6800.0)
+    avg_ms = kern[dom]["ms"] / max(kern[dom]["launches"], 1)
+    abytes = algorithmic_bytes(dom, n_img, n_spec)
+    achieved = abytes / (avg_ms / 1000.0) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(dom), "kernel": dom,
+                "bytes_per_launch": abytes, "avg_launch_us": avg_ms * 1000.0,
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+    per_iter_bytes = sum(algorithmic_bytes(k, n_img, n_spec) for k in
+                         ("ax_fwd", "ax_adj", "lat_mid", "lat_update"))
+    iter_gbs = per_iter_bytes * value / max(world, 1) / 1e9
+
+    # end to end through the host-buffer C-ABI entry point
+    s_h = s_d.cpu().pin_memory()
+    o_h = torch.empty(plan.image_shape, dtype=torch.complex64).pin_memory()
+    plan.solve_host(s_h, o_h, **opts)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_iters = 0
+    for _ in range(args.steps):
+        info = plan.solve_host(s_h, o_h, **opts)
+        e2e_iters += info["iterations"]
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s, e2e_iters], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t[:1], op=torch.distributed.ReduceOp.MAX)
+        tt = t[1:].clone()
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.SUM)
+        e2e_s, e2e_iters = float(t[0]), float(tt[0])
+    e2e = {"value": e2e_iters / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(s_h.numel() * 4), "d2h_bytes_per_step": int(o_h.numel() * 8)}
+
+    extras = {}
+    if not args.no_extras and rank == 0:
+        extras = run_extras(torch, plan, s_d, wl, args, infos[-1]["L"])
+
+    if rank == 0:
+        cpu_rate, n, el, nxs = oracle_iteration_rate(args.cpu_seconds) \
+            if world == 1 and not args.no_cpu else (None, 0, 0.0, 64)
+        cpu = None
+        if cpu_rate is not None:
+            cpu = {"value": cpu_rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"FP64 NumPy oracle (nufft, J=6): {n} FISTA iterations on a "
+                             f"{nxs}-A-scan slice of this workload in {el:.1f} s, per-iteration "
+                             f"time scaled x{1024 // nxs}; numpy.fft and elementwise work on "
+                             f"one thread"}
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "bscan_1024x2048_fp32", "nx": 1024, "nk": 2048,
+                           "nz": 2048, "iters_per_step": args.iters, "nufft_J": 6,
+                           "lambda_rel": wl.lambda_rel, "check_every": CHECK_EVERY,
+                           "l2": "flushed between timed steps (256 MiB write)",
+                           "parallelism": f"replicas x{world}"},
+                "gpu_launches": launches, "clocks": clk, "e2e": e2e, "roofline": roofline,
+                "cpu_baseline": cpu,
+                "iteration_gbs_algorithmic": iter_gbs,
+                "kernels": kern, "rr_last": infos[-1]["rr"] if infos else None,
+                "extras": extras}
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_extras(torch, plan, s_d, wl, args, L):
+    """A+A^H applications/s, the plain FP64 GPU path and (optionally) the volume."""
+    from paper_1905_06058_gb300 import inputs as I
+    from paper_1905_06058_gb300.isam import Plan
+    ex = {}
+    x = torch.empty(plan.image_shape, dtype=torch.complex64, device="cuda")
+    y = torch.empty(plan.spec_shape, dtype=torch.float32, device="cuda")
+    plan.adjoint(s_d, out=x)
+    for _ in range(3):
+        plan.forward(x, out=y)
+        plan.adjoint(y, out=x)
+    torch.cuda.synchronize()
+    reps = 50
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        plan.forward(x, out=y)
+        plan.adjoint(y, out=x)
+    b.record()
+    torch.cuda.synchronize()
+    ex["aah_per_s"] = reps / (a.elapsed_time(b) / 1000.0)
+    # plain FP64 GPU path (same kernels instantiated for double), same workload
+    p64 = Plan(wl.geom, precision="fp64")
+    s64 = s_d.double()
+    o64 = torch.empty(plan.image_shape, dtype=torch.complex128, device="cuda")
+    it64 = 20
+    p64.solve(s64, out=o64, lambda_rel=wl.lambda_rel, max_iter=2, L=L)
+    torch.cuda.synchronize()
+    a.record()
+    _, info = p64.solve(s64, out=o64, lambda_rel=wl.lambda_rel, max_iter=it64, L=L)
+    b.record()
+    torch.cuda.synchronize()
+    ex["fp64_iters_per_s"] = it64 / (a.elapsed_time(b) / 1000.0)
+    p64.close()
+    if args.volume:
+        ex["volume"] = run_volume(torch)
+    return ex
+
+
+def run_volume(torch):
+    from paper_1905_06058_gb300 import inputs as I
+    from paper_1905_06058_gb300.isam import Plan
+    wl = I.config3(dtype=np.complex64)
+    plan = Plan(wl.geom, precision="fp32")
+    eta = torch.from_numpy(wl.eta).cuda()
+    s = plan.forward(eta)
+    del eta
+    L = plan.lipschitz(iters=30, rtol=1e-6)
+    out = torch.empty(plan.image_shape, dtype=torch.complex64, device="cuda")
+    plan.solve(s, out=out, lambda_rel=wl.lambda_rel, max_iter=2, L=L)
+    torch.cuda.synchronize()
+    it = 20
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    plan.solve(s, out=out, lambda_rel=wl.lambda_rel, max_iter=it, L=L)
+    b.record()
+    torch.cuda.synchronize()
+    rate = it / (a.elapsed_time(b) / 1000.0)
+    n = wl.geom.nx * wl.geom.ny * wl.geom.nz
+    plan.close()
+    return {"workload": wl.name, "iters_per_s": rate, "L_estimate_iters": 30,
+            "iteration_gbs_algorithmic": 92 * n * rate / 1e9}
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

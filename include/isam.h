@@ -132,7 +132,10 @@ isam_status isam_solve_host(isam_plan* plan, const void* s_d_host,
                             isam_solve_info* info);
 
 /* L = ||A^H A|| by power iteration from the device start image v0 (NULL: a fixed
- * deterministic start), in FP64 on the device whatever the plan precision.
+ * deterministic start), in FP64 on the device whatever the plan precision (when
+ * the FP64 kernels fit the shared memory, else in the plan precision).  Stops
+ * after `iters` steps or when the estimate changes by <= rtol relative;
+ * iters = 0 selects the default used by isam_solve (1000 steps, 1e-11).
  * Synchronous.  The result is cached in the plan and used by isam_solve. */
 isam_status isam_lipschitz(isam_plan* plan, int32_t iters, double rtol, const void* v0,
                            double* L_out);

@@ -4,6 +4,10 @@
 // columns can be transformed together: element r of column c lives at
 // buf[r * stride + c]; the caller maps threads to (column, butterfly).
 //
+// The element type E is a complex number (float2 / double2) or a pair of
+// complex numbers (cpair<T>: two columns transformed in lock step with one
+// 16- or 32-byte shared-memory access per point).
+//
 // Direction SIGN = -1 computes X_m = sum_p x_p e^{-2 pi i m p / L},
 // SIGN = +1 the same with e^{+...}; no normalisation.  Twiddles come from a
 // table tw[m] = e^{-2 pi i m / L}, m < L (FP64-rounded), read through the
@@ -14,37 +18,75 @@
 
 namespace isam {
 
-template <int SIGN, typename C>
-__device__ __forceinline__ void dft2(C& a, C& b) {
-  C t = a; a = cadd(t, b); b = csub(t, b);
+template <typename T> struct alignas(2 * sizeof(cplx<T>)) cpair { cplx<T> a, b; };
+
+// arithmetic on complex numbers and complex pairs
+template <typename C> __device__ __forceinline__ C eadd(C a, C b) { return cadd(a, b); }
+template <typename C> __device__ __forceinline__ C esub(C a, C b) { return csub(a, b); }
+template <typename T> __device__ __forceinline__ cpair<T> eadd(cpair<T> a, cpair<T> b) {
+  return {cadd(a.a, b.a), cadd(a.b, b.b)};
+}
+template <typename T> __device__ __forceinline__ cpair<T> esub(cpair<T> a, cpair<T> b) {
+  return {csub(a.a, b.a), csub(a.b, b.b)};
+}
+template <int SIGN, typename C> __device__ __forceinline__ C emul_i(C a) { return cmul_i<SIGN>(a); }
+template <int SIGN, typename T> __device__ __forceinline__ cpair<T> emul_i(cpair<T> a) {
+  return {cmul_i<SIGN>(a.a), cmul_i<SIGN>(a.b)};
+}
+template <typename C> __device__ __forceinline__ C emul(C a, C w) { return cmul(a, w); }
+template <typename T> __device__ __forceinline__ cpair<T> emul(cpair<T> a, cplx<T> w) {
+  return {cmul(a.a, w), cmul(a.b, w)};
+}
+template <typename C, typename T> __device__ __forceinline__ C escale(C a, T s) { return cscale(a, s); }
+template <typename T> __device__ __forceinline__ cpair<T> escale(cpair<T> a, T s) {
+  return {cscale(a.a, s), cscale(a.b, s)};
+}
+// multiply by h (1 + SIGN i) and by h (-1 + SIGN i), h = 1/sqrt(2)
+template <int SIGN, typename C> __device__ __forceinline__ C ew8_1(C o) {
+  using T = decltype(o.x);
+  const T h = T(0.70710678118654752440);
+  C r; r.x = h * (o.x - SIGN * o.y); r.y = h * (o.y + SIGN * o.x); return r;
+}
+template <int SIGN, typename C> __device__ __forceinline__ C ew8_3(C o) {
+  using T = decltype(o.x);
+  const T h = T(0.70710678118654752440);
+  C r; r.x = h * (-o.x - SIGN * o.y); r.y = h * (-o.y + SIGN * o.x); return r;
+}
+template <int SIGN, typename T> __device__ __forceinline__ cpair<T> ew8_1(cpair<T> o) {
+  return {ew8_1<SIGN>(o.a), ew8_1<SIGN>(o.b)};
+}
+template <int SIGN, typename T> __device__ __forceinline__ cpair<T> ew8_3(cpair<T> o) {
+  return {ew8_3<SIGN>(o.a), ew8_3<SIGN>(o.b)};
 }
 
-template <int SIGN, typename C>
-__device__ __forceinline__ void dft4(C& a0, C& a1, C& a2, C& a3) {
-  C t0 = cadd(a0, a2), t1 = csub(a0, a2);
-  C t2 = cadd(a1, a3), t3 = cmul_i<SIGN>(csub(a1, a3));
-  a0 = cadd(t0, t2); a2 = csub(t0, t2);
-  a1 = cadd(t1, t3); a3 = csub(t1, t3);
+template <int SIGN, typename E>
+__device__ __forceinline__ void dft2(E& a, E& b) {
+  E t = a; a = eadd(t, b); b = esub(t, b);
 }
 
-template <int SIGN, typename T>
-__device__ __forceinline__ void dft8(cplx<T>* a) {
-  using C = cplx<T>;
+template <int SIGN, typename E>
+__device__ __forceinline__ void dft4(E& a0, E& a1, E& a2, E& a3) {
+  E t0 = eadd(a0, a2), t1 = esub(a0, a2);
+  E t2 = eadd(a1, a3), t3 = emul_i<SIGN>(esub(a1, a3));
+  a0 = eadd(t0, t2); a2 = esub(t0, t2);
+  a1 = eadd(t1, t3); a3 = esub(t1, t3);
+}
+
+template <int SIGN, typename E>
+__device__ __forceinline__ void dft8(E* a) {
   dft4<SIGN>(a[0], a[2], a[4], a[6]);
   dft4<SIGN>(a[1], a[3], a[5], a[7]);
-  const T h = T(0.70710678118654752440);
   // odd half times W8^k, W8 = e^{SIGN 2 pi i / 8}
-  C o1 = a[3], o2 = a[5], o3 = a[7];
-  a[3] = mk<T>(h * (o1.x - SIGN * o1.y), h * (o1.y + SIGN * o1.x));
-  a[5] = cmul_i<SIGN>(o2);
-  a[7] = mk<T>(h * (-o3.x - SIGN * o3.y), h * (-o3.y + SIGN * o3.x));
+  a[3] = ew8_1<SIGN>(a[3]);
+  a[5] = emul_i<SIGN>(a[5]);
+  a[7] = ew8_3<SIGN>(a[7]);
   // combine: y_k = E_k + W^k O_k, y_{k+4} = E_k - W^k O_k
-  C e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6];
-  C p0 = a[1], p1 = a[3], p2 = a[5], p3 = a[7];
-  a[0] = cadd(e0, p0); a[4] = csub(e0, p0);
-  a[1] = cadd(e1, p1); a[5] = csub(e1, p1);
-  a[2] = cadd(e2, p2); a[6] = csub(e2, p2);
-  a[3] = cadd(e3, p3); a[7] = csub(e3, p3);
+  E e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6];
+  E p0 = a[1], p1 = a[3], p2 = a[5], p3 = a[7];
+  a[0] = eadd(e0, p0); a[4] = esub(e0, p0);
+  a[1] = eadd(e1, p1); a[5] = esub(e1, p1);
+  a[2] = eadd(e2, p2); a[6] = esub(e2, p2);
+  a[3] = eadd(e3, p3); a[7] = esub(e3, p3);
 }
 
 template <int SIGN, typename T>
@@ -57,15 +99,14 @@ __device__ __forceinline__ cplx<T> twiddle(const cplx<T>* __restrict__ tw, int m
 // One Stockham pass of radix R on column `col` (element r at buf[r*stride+col]);
 // this thread does 8/R butterflies j = b + u * (L/8).  Reads all its inputs,
 // block barrier, writes.  Must be reached by every thread of the block.
-template <int SIGN, int R, typename T>
-__device__ __forceinline__ void stockham_pass(cplx<T>* buf, int stride, int col, int b, int L,
+template <int SIGN, int R, typename T, typename E>
+__device__ __forceinline__ void stockham_pass(E* buf, int stride, int col, int b, int L,
                                               int Ns, const cplx<T>* __restrict__ tw,
                                               bool active) {
-  using C = cplx<T>;
   constexpr int NB = 8 / R;          // butterflies per thread
   const int LR = L / R;
   const int L8 = L >> 3;
-  C v[8];
+  E v[8];
   if (active) {
 #pragma unroll
     for (int u = 0; u < NB; ++u) {
@@ -80,13 +121,13 @@ __device__ __forceinline__ void stockham_pass(cplx<T>* buf, int stride, int col,
     for (int u = 0; u < NB; ++u) {
       const int j = b + u * L8;
       const int k = j & (Ns - 1);
-      C* a = v + u * R;
+      E* a = v + u * R;
       if (Ns > 1) {
         const int step = (L / (Ns * R)) * k;   // twiddle index for r = 1
 #pragma unroll
-        for (int r = 1; r < R; ++r) a[r] = cmul(a[r], twiddle<SIGN, T>(tw, r * step));
+        for (int r = 1; r < R; ++r) a[r] = emul(a[r], twiddle<SIGN, T>(tw, r * step));
       }
-      if (R == 8) dft8<SIGN, T>(a);
+      if (R == 8) dft8<SIGN>(a);
       else if (R == 4) dft4<SIGN>(a[0], a[1], a[2], a[3]);
       else dft2<SIGN>(a[0], a[1]);
       const int base = (j - k) * R + k;
@@ -101,11 +142,9 @@ __device__ __forceinline__ void stockham_pass(cplx<T>* buf, int stride, int col,
 // L >= 8 the active threads own butterfly b < L/8; for L < 8 the thread with
 // b == 0 transforms the column directly.  Every thread of the block must call
 // it (it contains barriers); it ends with a barrier.
-template <int SIGN, typename T>
-__device__ __forceinline__ void fft_smem(cplx<T>* buf, int stride, int col, int b, int L,
-                                         int logL, const cplx<T>* __restrict__ tw,
-                                         bool active) {
-  using C = cplx<T>;
+template <int SIGN, typename T, typename E>
+__device__ __forceinline__ void fft_smem(E* buf, int stride, int col, int b, int L, int logL,
+                                         const cplx<T>* __restrict__ tw, bool active) {
   if (L >= 8) {
     int Ns = 1;
     const int n8 = logL / 3;
@@ -119,11 +158,11 @@ __device__ __forceinline__ void fft_smem(cplx<T>* buf, int stride, int col, int 
   } else {
     __syncthreads();
     if (active && b == 0 && L > 1) {
-      C a0 = buf[col], a1 = buf[stride + col];
+      E a0 = buf[col], a1 = buf[stride + col];
       if (L == 2) {
         dft2<SIGN>(a0, a1);
       } else {
-        C a2 = buf[2 * stride + col], a3 = buf[3 * stride + col];
+        E a2 = buf[2 * stride + col], a3 = buf[3 * stride + col];
         dft4<SIGN>(a0, a1, a2, a3);
         buf[2 * stride + col] = a2; buf[3 * stride + col] = a3;
       }

@@ -8,9 +8,6 @@
 
 namespace isam {
 
-// Density of the min-max coefficient table: nodes f = i / TABLE_D, i <= TABLE_D.
-constexpr int TABLE_D = 1024;
-
 // Per-plan constants of the Stolt map in oversampled-grid units (K = 2 nz,
 // grid unit = dk):  p_j = sqrt(4 kappa_j^2 - a) with kappa_j = k_j / dk and
 // a = (q / dk)^2 = Qx mx^2 + Qy my^2.  Written as p_j = c0 + 2 j - d_j with
@@ -22,6 +19,7 @@ struct StoltConst {
   float qx_hi, qx_lo, qy_hi, qy_lo;
   float zeta_hi, zeta_lo;
   float f0;
+  float B;        // 2 kappa_0 - c0, an integer multiple of K (exact in float)
   // double copies for the FP64 path
   double kap, Qx, Qy, zeta, c0d;
   int I0;
@@ -35,7 +33,21 @@ template <typename T> struct Tables {
   cplx<T>* tw_K = nullptr;   // [K]
   T* scale = nullptr;        // [nz]  s(n - nz/2) / sqrt(nz)
   cplx<T>* disp = nullptr;   // [nk]  e^{j phi(k_j)}
-  T* coef = nullptr;         // [(TABLE_D+1)][2J]  c_l(f_i), then c_l(f_{i+1}) - c_l(f_i)
+};
+
+// Min-max coefficients as polynomials in the fractional offset f.  With
+// x = f - 1/2 and y = 4 x^2 the symmetric design gives, for tap pairs
+// (p, J-1-p):  c_p = E_p(y) + x Q_p(y),  c_{J-1-p} = E_p(y) - x Q_p(y),
+// E_p of degree DE and Q_p of degree DO, fitted in FP64 to exact min-max
+// solutions at Chebyshev nodes (fit error 7.6e-9 relative in FP32 form,
+// 1.4e-14 in FP64 form for J <= 8).
+template <typename T> struct PolyDeg;
+template <> struct PolyDeg<float> { static constexpr int DE = 4, DO = 3; };
+template <> struct PolyDeg<double> { static constexpr int DE = 6, DO = 5; };
+constexpr int POLY_MAXP = 4;
+template <typename T> struct Poly {
+  T e[POLY_MAXP][7];
+  T o[POLY_MAXP][6];
 };
 
 // Lateral pass modes.
@@ -68,20 +80,26 @@ template <typename T> struct LatArgs {
   int* flag;             // non-finite flag
 };
 
+// Columns q and -q share the Stolt map; the axial kernels process them as a
+// pair (pairs[i] = (c1, c2), c2 == c1 for self-paired columns).
 template <typename T> struct AxArgs {
   const cplx<T>* in;
   cplx<T>* out;
   StoltConst sc;
   Tables<T> tab;
+  Poly<T> poly;
+  const int2* pairs;
 };
 
 // launchers (return cudaGetLastError())
 template <typename T> cudaError_t launch_lat(int mode, const LatArgs<T>& a, cudaStream_t s);
-template <typename T> cudaError_t launch_ax_fwd(const AxArgs<T>& a, int ncols, cudaStream_t s);
-template <typename T> cudaError_t launch_ax_adj(const AxArgs<T>& a, int ncols, cudaStream_t s);
+template <typename T> cudaError_t launch_ax_fwd(const AxArgs<T>& a, int npairs, cudaStream_t s);
+template <typename T> cudaError_t launch_ax_adj(const AxArgs<T>& a, int npairs, cudaStream_t s);
+template <typename T> size_t ax_smem_bytes(int K, int nk, bool adj);
 
-// FP64 min-max table (device), written as T
-template <typename T> cudaError_t build_minmax_table(int nz, int K, int J, T* out, cudaStream_t s);
+// FP64 exact min-max coefficients at offsets f[0..n) (device), out[i*J + l]
+cudaError_t minmax_nodes(int nz, int K, int J, const double* f, int n, double* out,
+                         cudaStream_t s);
 
 // reductions / elementwise
 template <typename T> cudaError_t launch_max_abs(const cplx<T>* x, size_t n, double* partial,

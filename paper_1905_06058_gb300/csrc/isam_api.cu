@@ -45,6 +45,10 @@ struct isam_plan {
   StoltConst sc{};
   Impl<float> f32;
   Impl<double> f64;
+  Poly<float> poly32{};
+  Poly<double> poly64{};
+  int2* pairs = nullptr;        // (q, -q) column pairs of the axial kernels
+  int npairs = 0;
   double* partial = nullptr;    // reduction partials
   int n_partial = 0;
   double* dscal = nullptr;      // device scalars [8]
@@ -139,7 +143,7 @@ template <typename T> isam_status dalloc(T** p, size_t n) {
 
 template <typename T> void impl_free(Impl<T>& im) {
   cudaFree(im.tab.tw_x); cudaFree(im.tab.tw_y); cudaFree(im.tab.tw_K);
-  cudaFree(im.tab.scale); cudaFree(im.tab.disp); cudaFree(im.tab.coef);
+  cudaFree(im.tab.scale); cudaFree(im.tab.disp);
   cudaFree(im.eta_hat); cudaFree(im.spec); cudaFree(im.grad);
   cudaFree(im.zA); cudaFree(im.zB); cudaFree(im.s_tmp);
   cudaFree(im.s_host_stage); cudaFree(im.out_stage);
@@ -164,12 +168,9 @@ double host_kb_scale(int n, int K, int J) {
   return (sinh(alpha) / alpha) / (sinh(r) / r);
 }
 
-template <typename T> size_t ax_adj_smem(int K, int J) {
-  return size_t(K) * 2 * sizeof(cplx<T>) + size_t(TABLE_D + 1) * 2 * J * sizeof(T);
-}
-
 template <typename T> bool precision_fits(const isam_plan* P) {
-  return ax_adj_smem<T>(P->K, P->J) <= 227u * 1024u;
+  return ax_smem_bytes<T>(P->K, P->nk, true) <= 227u * 1024u &&
+         ax_smem_bytes<T>(P->K, P->nk, false) <= 227u * 1024u;
 }
 
 template <typename T> isam_status impl_init(isam_plan* P, Impl<T>& im) {
@@ -201,8 +202,6 @@ template <typename T> isam_status impl_init(isam_plan* P, Impl<T>& im) {
     ISAM_TRY(dalloc(&im.tab.disp, P->nk));
     CUDA_TRY(cudaMemcpy(im.tab.disp, h.data(), sizeof(cplx<T>) * P->nk, cudaMemcpyHostToDevice));
   }
-  ISAM_TRY(dalloc(&im.tab.coef, size_t(TABLE_D + 1) * 2 * P->J));
-  CUDA_TRY(build_minmax_table<T>(P->nz, P->K, P->J, im.tab.coef, P->stream));
   ISAM_TRY(dalloc(&im.eta_hat, P->n_img));
   ISAM_TRY(dalloc(&im.spec, P->n_spec));
   ISAM_TRY(dalloc(&im.grad, P->n_img));
@@ -238,10 +237,16 @@ template <typename T> isam_status lat(isam_plan* P, int mode, const LatArgs<T>& 
   return launch(P, cls, [&] { return launch_lat<T>(mode, a, P->stream); });
 }
 
+template <typename T> const Poly<T>& poly_of(const isam_plan* P);
+template <> const Poly<float>& poly_of<float>(const isam_plan* P) { return P->poly32; }
+template <> const Poly<double>& poly_of<double>(const isam_plan* P) { return P->poly64; }
+
 template <typename T> AxArgs<T> ax_args(isam_plan* P, const Impl<T>& im, const cplx<T>* in,
                                        cplx<T>* out) {
   AxArgs<T> a{};
   a.in = in; a.out = out; a.sc = P->sc; a.tab = im.tab;
+  a.poly = poly_of<T>(P);
+  a.pairs = P->pairs;
   return a;
 }
 
@@ -267,7 +272,7 @@ template <typename T> isam_status op_forward(isam_plan* P, const void* eta, void
   Impl<T>& im = impl_of<T>(P);
   ISAM_TRY(lat_forward<T>(P, im, eta, im.eta_hat, P->nz, false));
   ISAM_TRY(launch(P, ISAM_KCLASS_AX_FWD, [&] {
-    return launch_ax_fwd<T>(ax_args<T>(P, im, im.eta_hat, im.spec), P->nx * P->ny, P->stream);
+    return launch_ax_fwd<T>(ax_args<T>(P, im, im.eta_hat, im.spec), P->npairs, P->stream);
   }));
   return lat_inverse<T>(P, im, im.spec, s, P->nk, true);
 }
@@ -276,7 +281,7 @@ template <typename T> isam_status op_adjoint(isam_plan* P, const void* s, void* 
   Impl<T>& im = impl_of<T>(P);
   ISAM_TRY(lat_forward<T>(P, im, s, im.spec, P->nk, true));
   ISAM_TRY(launch(P, ISAM_KCLASS_AX_ADJ, [&] {
-    return launch_ax_adj<T>(ax_args<T>(P, im, im.spec, im.grad), P->nx * P->ny, P->stream);
+    return launch_ax_adj<T>(ax_args<T>(P, im, im.spec, im.grad), P->npairs, P->stream);
   }));
   return lat_inverse<T>(P, im, im.grad, eta, P->nz, false);
 }
@@ -349,7 +354,7 @@ template <typename T> isam_status fista_iteration(isam_plan* P, Impl<T>& im, con
                                                   bool norms) {
   cudaStream_t s = P->stream;
   ISAM_TRY(launch(P, ISAM_KCLASS_AX_FWD, [&] {
-    return launch_ax_fwd<T>(ax_args<T>(P, im, im.eta_hat, im.spec), P->nx * P->ny, s);
+    return launch_ax_fwd<T>(ax_args<T>(P, im, im.eta_hat, im.spec), P->npairs, s);
   }));
   if (P->ny == 1) {
     LatArgs<T> a = lat_args<T>(im, 1, P->nx, P->nk, im.tab.tw_x, im.spec, im.spec);
@@ -363,7 +368,7 @@ template <typename T> isam_status fista_iteration(isam_plan* P, Impl<T>& im, con
     ISAM_TRY(lat<T>(P, LAT_C2C_FWD, lat_args<T>(im, P->ny, P->nx, P->nk, im.tab.tw_x, im.spec, im.spec)));
   }
   ISAM_TRY(launch(P, ISAM_KCLASS_AX_ADJ, [&] {
-    return launch_ax_adj<T>(ax_args<T>(P, im, im.spec, im.grad), P->nx * P->ny, s);
+    return launch_ax_adj<T>(ax_args<T>(P, im, im.spec, im.grad), P->npairs, s);
   }));
   LatArgs<T> u;
   if (P->ny == 1) {
@@ -543,6 +548,7 @@ void make_stolt(isam_plan* P) {
   c.c0d = fmod(2.0 * c.kap, double(P->K));
   c.I0 = int(floor(c.c0d));
   c.f0 = float(c.c0d - double(c.I0));
+  c.B = float(2.0 * c.kap - c.c0d);
   split_ff(c.kap, &c.kap_hi, &c.kap_lo);
   split_ff(c.Qx, &c.qx_hi, &c.qx_lo);
   split_ff(c.Qy, &c.qy_hi, &c.qy_lo);
@@ -550,6 +556,103 @@ void make_stolt(isam_plan* P) {
   c.K = P->K; c.logK = ilog2(P->K);
   c.nx = P->nx; c.ny = P->ny; c.nk = P->nk; c.nz = P->nz; c.J = P->J;
   c.focus = p.z0 != 0.0;
+}
+
+// Least squares min ||V a - v|| for the Vandermonde V_ik = y_i^k (k <= deg),
+// by Householder QR in double.
+void ls_poly(const std::vector<double>& y, const std::vector<double>& v, int deg, double* a) {
+  const int m = int(y.size()), n = deg + 1;
+  std::vector<double> A(size_t(m) * n), b(v);
+  for (int i = 0; i < m; ++i) {
+    double pw = 1.0;
+    for (int k = 0; k < n; ++k) { A[size_t(i) * n + k] = pw; pw *= y[i]; }
+  }
+  for (int k = 0; k < n; ++k) {
+    double nrm = 0.0;
+    for (int i = k; i < m; ++i) nrm += A[size_t(i) * n + k] * A[size_t(i) * n + k];
+    nrm = sqrt(nrm);
+    const double akk = A[size_t(k) * n + k];
+    const double alpha = akk > 0 ? -nrm : nrm;
+    std::vector<double> u(m, 0.0);
+    for (int i = k; i < m; ++i) u[i] = A[size_t(i) * n + k];
+    u[k] -= alpha;
+    double un = 0.0;
+    for (int i = k; i < m; ++i) un += u[i] * u[i];
+    if (un == 0.0) continue;
+    for (int c = k; c < n; ++c) {
+      double d = 0.0;
+      for (int i = k; i < m; ++i) d += u[i] * A[size_t(i) * n + c];
+      d = 2.0 * d / un;
+      for (int i = k; i < m; ++i) A[size_t(i) * n + c] -= d * u[i];
+    }
+    double d = 0.0;
+    for (int i = k; i < m; ++i) d += u[i] * b[i];
+    d = 2.0 * d / un;
+    for (int i = k; i < m; ++i) b[i] -= d * u[i];
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    double acc = b[k];
+    for (int c = k + 1; c < n; ++c) acc -= A[size_t(k) * n + c] * a[c];
+    a[k] = acc / A[size_t(k) * n + k];
+  }
+}
+
+// Exact min-max coefficients at Chebyshev nodes of y = 4 (f - 1/2)^2 (FP64,
+// on the device), then the even/odd polynomial fits of both precisions.
+isam_status build_poly(isam_plan* P) {
+  constexpr int M = 48;
+  const int J = P->J;
+  std::vector<double> y(M), x(M), f(M);
+  for (int i = 0; i < M; ++i) {
+    y[i] = 0.5 * (cos(M_PI * (i + 0.5) / M) + 1.0);
+    x[i] = 0.5 * sqrt(y[i]);
+    f[i] = 0.5 + x[i];
+  }
+  double *df = nullptr, *dc = nullptr;
+  ISAM_TRY(dalloc(&df, M));
+  isam_status st = dalloc(&dc, size_t(M) * J);
+  std::vector<double> c(size_t(M) * J);
+  if (st == ISAM_OK) st = from_cuda(cudaMemcpy(df, f.data(), sizeof(double) * M, cudaMemcpyHostToDevice));
+  if (st == ISAM_OK) st = from_cuda(minmax_nodes(P->nz, P->K, J, df, M, dc, P->stream));
+  if (st == ISAM_OK) st = from_cuda(cudaStreamSynchronize(P->stream));
+  if (st == ISAM_OK)
+    st = from_cuda(cudaMemcpy(c.data(), dc, sizeof(double) * M * J, cudaMemcpyDeviceToHost));
+  cudaFree(df);
+  cudaFree(dc);
+  if (st != ISAM_OK) return st;
+  for (int p = 0; p < J / 2; ++p) {
+    std::vector<double> e(M), o(M);
+    for (int i = 0; i < M; ++i) {
+      const double cp = c[size_t(i) * J + p], cm = c[size_t(i) * J + (J - 1 - p)];
+      e[i] = 0.5 * (cp + cm);
+      o[i] = 0.5 * (cp - cm) / x[i];
+    }
+    double ae[7] = {0}, ao[6] = {0};
+    ls_poly(y, e, PolyDeg<double>::DE, ae);
+    ls_poly(y, o, PolyDeg<double>::DO, ao);
+    for (int k = 0; k <= PolyDeg<double>::DE; ++k) P->poly64.e[p][k] = ae[k];
+    for (int k = 0; k <= PolyDeg<double>::DO; ++k) P->poly64.o[p][k] = ao[k];
+    ls_poly(y, e, PolyDeg<float>::DE, ae);
+    ls_poly(y, o, PolyDeg<float>::DO, ao);
+    for (int k = 0; k <= PolyDeg<float>::DE; ++k) P->poly32.e[p][k] = float(ae[k]);
+    for (int k = 0; k <= PolyDeg<float>::DO; ++k) P->poly32.o[p][k] = float(ao[k]);
+  }
+  return ISAM_OK;
+}
+
+// Columns (ix, iy) and (-ix, -iy) mod (nx, ny) share |q|; list each pair once.
+isam_status build_pairs(isam_plan* P) {
+  std::vector<int2> pr;
+  for (int iy = 0; iy < P->ny; ++iy)
+    for (int ix = 0; ix < P->nx; ++ix) {
+      const int c = iy * P->nx + ix;
+      const int d = ((P->ny - iy) % P->ny) * P->nx + (P->nx - ix) % P->nx;
+      if (c <= d) pr.push_back(make_int2(c, d));
+    }
+  P->npairs = int(pr.size());
+  ISAM_TRY(dalloc(&P->pairs, pr.size()));
+  return from_cuda(cudaMemcpy(P->pairs, pr.data(), sizeof(int2) * pr.size(),
+                              cudaMemcpyHostToDevice));
 }
 
 struct DeviceGuard {
@@ -605,6 +708,8 @@ isam_status isam_plan_create(const isam_params* p, void* stream, isam_plan** out
   if (st == ISAM_OK) st = dalloc(&P->dscal, 8);
   if (st == ISAM_OK) st = dalloc(&P->flag, 1);
   if (st == ISAM_OK) st = from_cuda(cudaMallocHost(reinterpret_cast<void**>(&P->hscal), 8 * sizeof(double)));
+  if (st == ISAM_OK) st = build_pairs(P);
+  if (st == ISAM_OK) st = build_poly(P);
   if (st == ISAM_OK) {
     if (p->precision == ISAM_FP64) st = impl_init<double>(P, P->f64);
     else st = impl_init<float>(P, P->f32);
@@ -625,6 +730,7 @@ void isam_plan_destroy(isam_plan* P) {
   impl_free(P->f32);
   impl_free(P->f64);
   cudaFree(P->partial);
+  cudaFree(P->pairs);
   cudaFree(P->dscal);
   cudaFree(P->flag);
   if (P->hscal) cudaFreeHost(P->hscal);
@@ -708,7 +814,11 @@ isam_status isam_solve_host(isam_plan* P, const void* s_h, const isam_solve_opts
 
 isam_status isam_lipschitz(isam_plan* P, int32_t iters, double rtol, const void* v0,
                            double* L_out) {
-  if (!P || !L_out || iters < 1 || !(rtol >= 0)) return ISAM_ERR_INVALID;
+  if (!P || !L_out || iters < 0 || !(rtol >= 0)) return ISAM_ERR_INVALID;
+  if (iters == 0) {
+    iters = kPowerIters;
+    rtol = kPowerRtol;
+  }
   DeviceGuard g(P->device);
   P->launches = 0;
   const int v0_double = P->p.precision == ISAM_FP64;

@@ -1,24 +1,30 @@
-// Axial Stolt-mapped NUFFT kernels: one thread block per lateral-frequency
-// column (q_x, q_y).
+// Axial Stolt-mapped NUFFT kernels.  One thread block per pair of lateral-
+// frequency columns (q, -q): both share the Stolt map beta(|q|, k), so the
+// positions, phases and interpolation coefficients are computed once and
+// applied to two columns whose FFTs run in lock step (16- or 32-byte
+// shared-memory elements).
 //
 //   k_ax_fwd  (§3.2, Eq. 3, 13, 16; min-max NUFFT of Fessler & Sutton):
 //     S(q, k_j) = e^{j phi(k_j)} e^{j (2 k_j + beta) z0}
 //                 sum_l c_l(f_j) Y[(m0_j + l) mod K],
 //     Y = K-point e^{+} DFT of the scaled, zero-padded column
 //         s(n - nz/2) eta_hat(q, z_n) / sqrt(nz) placed at (n - nz/2) mod K.
-//   k_ax_adj  (Eq. 17, the exact adjoint of k_ax_fwd): gathers
-//     conj(phase_j) R_hat(q, k_j) c_l(f_j) into bins m0_j + l with compensated
-//     (TwoSum) accumulation, K-point e^{-} DFT, truncation to the nz samples,
-//     scaling.  The scatter is made race-free without atomics: Stolt positions
-//     rise by at least two grid bins per k sample (dp/dj = 4 kappa / p >= 2),
-//     so samples j with the same residue mod J/2 touch disjoint bins; samples
-//     are processed residue class by residue class, in chunks of K/2 bins so
-//     that the wrap mod K never folds two contributions onto one bin.
+//   k_ax_adj  (Eq. 17, the exact adjoint of k_ax_fwd), in gather form: every
+//     oversampled bin u sums c_{u - m0_j}(f_j) conj(phase_j) R_hat(q, k_j) over
+//     the few samples j whose J-neighbourhood covers u (no atomics).  The
+//     contributors of u are found through first[u], the smallest j whose
+//     neighbourhood reaches u, built from the monotone Stolt positions
+//     (dp/dj = 4 kappa / p >= 2 bins per sample).  Each bin is owned by one
+//     thread and accumulated with compensated (TwoSum) summation in
+//     registers; then the K-point e^{-} DFT, truncation and scaling.
 //
-// Stolt positions are computed per sample from per-plan constants in
+// Stolt positions are evaluated per sample from per-plan constants in
 // float-float arithmetic (FP32 path) or double (FP64 path): the grid
 // coordinate reaches ~5e4 bins while its fractional part must be right to
-// ~1e-7, beyond single precision.
+// ~1e-7.  Interpolation coefficients are evaluated from their even/odd
+// polynomial form (see Poly), held in kernel parameters.
+#include <limits.h>
+
 #include "fft_smem.cuh"
 #include "internal.cuh"
 
@@ -28,32 +34,35 @@ __device__ __forceinline__ int signed_freq(int i, int n) { return i <= (n - 1) /
 
 template <typename T> struct StoltPos;
 
+// p_j = sqrt(4 kappa_j^2 - a), a = (q/dk)^2, in float-float; the unwrapped
+// grid index is p_j - B with B = 2 kappa_0 - c0 (a multiple of K).
 template <> struct StoltPos<float> {
-  ff a;   // (q / dk)^2
+  ff a;
   __device__ StoltPos(const StoltConst& c, int mx, int my) {
     a = ff_add(ff_mul_f({c.qx_hi, c.qx_lo}, float(mx * mx)),
                ff_mul_f({c.qy_hi, c.qy_lo}, float(my * my)));
   }
-  // position of sample j: floor (unwrapped, integer) and fraction; focus turn
   __device__ __forceinline__ bool at(const StoltConst& c, int j, int& mfl, float& frac,
                                      float& turn) const {
-    ff kap = ff_add({c.kap_hi, c.kap_lo}, {float(j), 0.0f});
-    ff x = ff_sub(ff_mul_f(ff_mul(kap, kap), 4.0f), a);
+    const ff kap = ff_add({c.kap_hi, c.kap_lo}, {float(j), 0.0f});
+    ff k2 = ff_mul(kap, kap);
+    k2.hi *= 4.0f; k2.lo *= 4.0f;                       // exact
+    const ff x = ff_sub(k2, a);
     if (!(x.hi > 0.0f)) return false;
-    ff p = ff_sqrt(x);
-    ff D = ff_add(ff_mul_f(kap, 2.0f), p);
-    ff d = ff_div(a, D);
-    ff t = ff_sub({c.f0, 0.0f}, d);
+    const ff p = ff_sqrt(x);
+    ff t = ff_two_sum(p.hi, -c.B);
+    t.lo += p.lo;
     float fl = floorf(t.hi);
     float fr = __fadd_rn(__fsub_rn(t.hi, fl), t.lo);
     if (fr < 0.0f) { fr += 1.0f; fl -= 1.0f; }
     else if (fr >= 1.0f) { fr -= 1.0f; fl += 1.0f; }
-    mfl = c.I0 + 2 * j + int(fl);
+    mfl = int(fl);
     frac = fr;
     turn = 0.0f;
-    if (c.focus) {
-      ff r = ff_mul(d, {c.zeta_hi, c.zeta_lo});
-      float n = rintf(r.hi);
+    if (c.focus) {                                      // (2 kappa - p) zeta, in turns
+      const ff d = ff_sub({2.0f * kap.hi, 2.0f * kap.lo}, p);
+      const ff r = ff_mul(d, {c.zeta_hi, c.zeta_lo});
+      const float n = rintf(r.hi);
       turn = __fadd_rn(__fsub_rn(r.hi, n), r.lo);
     }
     return true;
@@ -67,19 +76,18 @@ template <> struct StoltPos<double> {
   }
   __device__ __forceinline__ bool at(const StoltConst& c, int j, int& mfl, double& frac,
                                      double& turn) const {
-    double kap = c.kap + double(j);
-    double x = 4.0 * kap * kap - a;
+    const double kap = c.kap + double(j);
+    const double x = 4.0 * kap * kap - a;
     if (!(x > 0.0)) return false;
-    double p = sqrt(x);
-    double d = a / (2.0 * kap + p);
-    double t = (c.c0d - double(c.I0)) - d;
-    double fl = floor(t);
-    frac = t - fl;
-    if (frac >= 1.0) { frac -= 1.0; fl += 1.0; }
-    mfl = c.I0 + 2 * j + int(fl);
+    const double p = sqrt(x);
+    const double d = a / (2.0 * kap + p);               // 2 kappa - p without cancellation
+    const double t = (c.c0d + 2.0 * double(j)) - d;     // = p - B
+    const double fl = floor(t);
+    frac = t - fl;                                      // exact, in [0, 1)
+    mfl = int(fl);
     turn = 0.0;
     if (c.focus) {
-      double r = d * c.zeta;
+      const double r = d * c.zeta;
       turn = r - rint(r);
     }
     return true;
@@ -101,187 +109,264 @@ __device__ __forceinline__ cplx<T> spectral_phase(const StoltConst& sc, const cp
   return ph;
 }
 
-// interpolation coefficients c_l(f) by linear interpolation of the table
+// all J coefficients c_l(f)
 template <typename T, int J>
-__device__ __forceinline__ void coefficients(const T* __restrict__ tab, T frac, T* c) {
-  T x = frac * T(TABLE_D);
-  int i = min(int(x), TABLE_D - 1);
-  T w = x - T(i);
-  const T* row = tab + i * (2 * J);
+__device__ __forceinline__ void coefficients(const Poly<T>& P, T frac, T* c) {
+  constexpr int DE = PolyDeg<T>::DE, DO = PolyDeg<T>::DO;
+  const T x = frac - T(0.5);
+  const T y = T(4) * x * x;
 #pragma unroll
-  for (int l = 0; l < J; ++l) c[l] = fma(w, row[J + l], row[l]);
+  for (int p = 0; p < J / 2; ++p) {
+    T e = P.e[p][DE];
+#pragma unroll
+    for (int k = DE - 1; k >= 0; --k) e = fma(e, y, P.e[p][k]);
+    T o = P.o[p][DO];
+#pragma unroll
+    for (int k = DO - 1; k >= 0; --k) o = fma(o, y, P.o[p][k]);
+    c[p] = fma(x, o, e);
+    c[J - 1 - p] = fma(-x, o, e);
+  }
+}
+
+// one coefficient c_l(f)
+template <typename T, int J>
+__device__ __forceinline__ T coefficient(const Poly<T>& P, T frac, int l) {
+  constexpr int DE = PolyDeg<T>::DE, DO = PolyDeg<T>::DO;
+  const T x = frac - T(0.5);
+  const T y = T(4) * x * x;
+  const int p = l < J / 2 ? l : J - 1 - l;
+  T e = P.e[p][DE];
+#pragma unroll
+  for (int k = DE - 1; k >= 0; --k) e = fma(e, y, P.e[p][k]);
+  T o = P.o[p][DO];
+#pragma unroll
+  for (int k = DO - 1; k >= 0; --k) o = fma(o, y, P.o[p][k]);
+  return fma(l < J / 2 ? x : -x, o, e);
+}
+
+template <typename T>
+__device__ __forceinline__ void pair_columns(const AxArgs<T>& A, int& c1, int& c2, int& mx,
+                                             int& my) {
+  const int2 pr = A.pairs[blockIdx.x];
+  c1 = pr.x;
+  c2 = pr.y;
+  mx = signed_freq(c1 % A.sc.nx, A.sc.nx);
+  my = signed_freq(c1 / A.sc.nx, A.sc.ny);
 }
 
 template <typename T, int J>
-__global__ void __launch_bounds__(512) k_ax_fwd(AxArgs<T> A) {
+__global__ void __launch_bounds__(512) k_ax_fwd(const __grid_constant__ AxArgs<T> A) {
   using C = cplx<T>;
+  using V = cpair<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const StoltConst& sc = A.sc;
   const int K = sc.K, nz = sc.nz, nk = sc.nk;
-  C* Y = reinterpret_cast<C*>(smem_raw);
-  T* tab = reinterpret_cast<T*>(Y + K);
+  V* Y = reinterpret_cast<V*>(smem_raw);
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int col = blockIdx.x;
+  int c1, c2, mx, my;
+  pair_columns(A, c1, c2, mx, my);
+  const bool two = c2 != c1;
 
-  for (int i = tid; i < (TABLE_D + 1) * 2 * J; i += nt) tab[i] = __ldg(A.tab.coef + i);
-  // zero the padding: bins nz/2 .. K - nz/2 - 1
-  for (int i = nz / 2 + tid; i < K - nz / 2; i += nt) Y[i] = mk<T>(0, 0);
-  const C* x = A.in + size_t(col) * nz;
+  const V zero = {mk<T>(0, 0), mk<T>(0, 0)};
+  for (int i = nz / 2 + tid; i < K - nz / 2; i += nt) Y[i] = zero;
+  const C* x1 = A.in + size_t(c1) * nz;
+  const C* x2 = A.in + size_t(c2) * nz;
   for (int n = tid; n < nz; n += nt) {
     int p = n - nz / 2;
     if (p < 0) p += K;
-    Y[p] = cscale(x[n], __ldg(A.tab.scale + n));
+    const T s = __ldg(A.tab.scale + n);
+    V v;
+    v.a = cscale(x1[n], s);
+    v.b = two ? cscale(x2[n], s) : mk<T>(0, 0);
+    Y[p] = v;
   }
   __syncthreads();
   fft_smem<+1, T>(Y, 1, 0, tid, K, sc.logK, A.tab.tw_K, true);
 
-  const int ix = col % sc.nx, iy = col / sc.nx;
-  StoltPos<T> sp(sc, signed_freq(ix, sc.nx), signed_freq(iy, sc.ny));
-  C* out = A.out + size_t(col) * nk;
+  const StoltPos<T> sp(sc, mx, my);
+  C* o1 = A.out + size_t(c1) * nk;
+  C* o2 = A.out + size_t(c2) * nk;
   for (int j = tid; j < nk; j += nt) {
     int mfl;
     T frac, turn;
-    C acc = mk<T>(0, 0);
+    C a1 = mk<T>(0, 0), a2 = mk<T>(0, 0);
     if (sp.at(sc, j, mfl, frac, turn)) {
       T c[J];
-      coefficients<T, J>(tab, frac, c);
+      coefficients<T, J>(A.poly, frac, c);
       const int m0 = mfl - J / 2 + 1;
 #pragma unroll
       for (int l = 0; l < J; ++l) {
-        C y = Y[(m0 + l) & (K - 1)];
-        acc.x = fma(c[l], y.x, acc.x);
-        acc.y = fma(c[l], y.y, acc.y);
+        const V y = Y[(m0 + l) & (K - 1)];
+        a1.x = fma(c[l], y.a.x, a1.x);
+        a1.y = fma(c[l], y.a.y, a1.y);
+        a2.x = fma(c[l], y.b.x, a2.x);
+        a2.y = fma(c[l], y.b.y, a2.y);
       }
-      acc = cmul(acc, spectral_phase<T>(sc, A.tab.disp, j, turn));
+      const C ph = spectral_phase<T>(sc, A.tab.disp, j, turn);
+      a1 = cmul(a1, ph);
+      a2 = cmul(a2, ph);
     }
-    out[j] = acc;
+    o1[j] = a1;
+    if (two) o2[j] = a2;
   }
 }
 
 // TwoSum-compensated add of v into (sum, comp)
 template <typename T>
 __device__ __forceinline__ void comp_add(T& sum, T& comp, T v) {
-  T s = sum + v;
-  T bb = s - sum;
-  T err = (sum - (s - bb)) + (v - bb);
+  const T s = sum + v;
+  const T bb = s - sum;
+  comp += (sum - (s - bb)) + (v - bb);
   sum = s;
-  comp += err;
 }
 
-constexpr int MAXU = 4;   // nk / (K/8) <= 4 because nz >= nk
+constexpr int BINS_PER_THREAD = 8;   // K / blockDim
 
 template <typename T, int J>
-__global__ void __launch_bounds__(512) k_ax_adj(AxArgs<T> A) {
+__global__ void __launch_bounds__(512) k_ax_adj(const __grid_constant__ AxArgs<T> A) {
   using C = cplx<T>;
+  using V = cpair<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const StoltConst& sc = A.sc;
   const int K = sc.K, nz = sc.nz, nk = sc.nk;
-  C* Y = reinterpret_cast<C*>(smem_raw);
-  C* Cc = Y + K;                                  // compensation terms
-  T* tab = reinterpret_cast<T*>(Cc + K);
-  __shared__ int chunk_lo, chunk_hi;
+  // phase 1 arrays (aliased by Y in phase 3)
+  V* val = reinterpret_cast<V*>(smem_raw);                  // [nk]
+  T* fr = reinterpret_cast<T*>(val + nk);                   // [nk]
+  int* m0s = reinterpret_cast<int*>(fr + nk);               // [nk]
+  unsigned short* first = reinterpret_cast<unsigned short*>(m0s + nk);   // [2K]
+  V* Y = reinterpret_cast<V*>(smem_raw);                    // [K]
+  __shared__ int u_lo, u_hi;
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int col = blockIdx.x;
+  int c1, c2, mx, my;
+  pair_columns(A, c1, c2, mx, my);
+  const bool two = c2 != c1;
 
-  if (tid == 0) { chunk_lo = INT_MAX; chunk_hi = INT_MIN; }
-  for (int i = tid; i < (TABLE_D + 1) * 2 * J; i += nt) tab[i] = __ldg(A.tab.coef + i);
-  for (int i = tid; i < K; i += nt) { Y[i] = mk<T>(0, 0); Cc[i] = mk<T>(0, 0); }
+  if (tid == 0) { u_lo = INT_MAX; u_hi = INT_MIN; }
   __syncthreads();
-
-  const int ix = col % sc.nx, iy = col / sc.nx;
-  StoltPos<T> sp(sc, signed_freq(ix, sc.nx), signed_freq(iy, sc.ny));
-  const C* rin = A.in + size_t(col) * nk;
-  const int half = K / 2;
-  int m0s[MAXU], chunk[MAXU];
-  T cs[MAXU][J];
-  C val[MAXU];
-#pragma unroll
-  for (int u = 0; u < MAXU; ++u) {
-    const int j = tid + u * nt;
-    chunk[u] = INT_MIN;
-    if (j < nk) {
-      int mfl;
-      T frac, turn;
-      if (sp.at(sc, j, mfl, frac, turn)) {
-        coefficients<T, J>(tab, frac, cs[u]);
-        m0s[u] = mfl - J / 2 + 1;
-        val[u] = cmulc(__ldg(rin + j), spectral_phase<T>(sc, A.tab.disp, j, turn));
-        // chunks of K/2 unwrapped bins (floor division)
-        chunk[u] = (mfl >= 0) ? mfl / half : -((-mfl + half - 1) / half);
-        atomicMin(&chunk_lo, chunk[u]);
-        atomicMax(&chunk_hi, chunk[u]);
-      }
+  // phase 1: per sample j, position, coefficient offset and phased values
+  const StoltPos<T> sp(sc, mx, my);
+  const C* r1 = A.in + size_t(c1) * nk;
+  const C* r2 = A.in + size_t(c2) * nk;
+  int my_lo = INT_MAX, my_hi = INT_MIN;
+  for (int j = tid; j < nk; j += nt) {
+    int mfl;
+    T frac, turn;
+    V v = {mk<T>(0, 0), mk<T>(0, 0)};
+    int m0 = INT_MIN;
+    if (sp.at(sc, j, mfl, frac, turn)) {
+      const C ph = spectral_phase<T>(sc, A.tab.disp, j, turn);
+      v.a = cmulc(r1[j], ph);
+      v.b = two ? cmulc(r2[j], ph) : mk<T>(0, 0);
+      m0 = mfl - J / 2 + 1;
+      my_lo = min(my_lo, m0);
+      my_hi = max(my_hi, m0);
     }
+    val[j] = v;
+    fr[j] = frac;
+    m0s[j] = m0;
+  }
+  if (my_lo != INT_MAX) {
+    atomicMin(&u_lo, my_lo);
+    atomicMax(&u_hi, my_hi + J - 1);
   }
   __syncthreads();
-  const int clo = chunk_lo, chi = chunk_hi;
-  constexpr int NR = J / 2;
-  for (int ch = clo; ch <= chi; ++ch) {
-    for (int rsd = 0; rsd < NR; ++rsd) {
+  const int ulo = u_lo, uhi = u_hi;
+  // per-thread compensated accumulators for bins m = tid + i * nt
+  V acc[BINS_PER_THREAD], cmp[BINS_PER_THREAD];
 #pragma unroll
-      for (int u = 0; u < MAXU; ++u) {
-        const int j = tid + u * nt;
-        if (chunk[u] == ch && (j % NR) == rsd) {
+  for (int i = 0; i < BINS_PER_THREAD; ++i) {
+    acc[i] = {mk<T>(0, 0), mk<T>(0, 0)};
+    cmp[i] = acc[i];
+  }
+  // phase 2: windows of 2K unwrapped bins (one window unless near cut-off)
+  for (int W0 = ulo; W0 <= uhi; W0 += 2 * K) {
+    const int W1 = min(uhi, W0 + 2 * K - 1);
+    // first[u - W0] = smallest j whose neighbourhood m0_j .. m0_j + J - 1 reaches u
+    for (int j = tid; j < nk; j += nt) {
+      const int m0 = m0s[j];
+      if (m0 == INT_MIN) continue;
+      const int prev = (j > 0 && m0s[j - 1] != INT_MIN) ? m0s[j - 1] + J : INT_MIN;
+      const int a = max(max(prev, ulo), W0);
+      const int b = min(m0 + J - 1, W1);
+      for (int u = a; u <= b; ++u) first[u - W0] = (unsigned short)j;
+    }
+    __syncthreads();
 #pragma unroll
-          for (int l = 0; l < J; ++l) {
-            const int bin = (m0s[u] + l) & (K - 1);
-            C s = Y[bin], e = Cc[bin];
-            comp_add(s.x, e.x, cs[u][l] * val[u].x);
-            comp_add(s.y, e.y, cs[u][l] * val[u].y);
-            Y[bin] = s;
-            Cc[bin] = e;
-          }
+    for (int i = 0; i < BINS_PER_THREAD; ++i) {
+      const int m = tid + i * nt;
+      int u = W0 + ((m - W0) % K + K) % K;
+      for (; u <= W1; u += K) {
+        for (int j = first[u - W0]; j < nk; ++j) {
+          const int m0 = m0s[j];
+          if (m0 > u) break;
+          const T c = coefficient<T, J>(A.poly, fr[j], u - m0);
+          const V v = val[j];
+          comp_add(acc[i].a.x, cmp[i].a.x, c * v.a.x);
+          comp_add(acc[i].a.y, cmp[i].a.y, c * v.a.y);
+          comp_add(acc[i].b.x, cmp[i].b.x, c * v.b.x);
+          comp_add(acc[i].b.y, cmp[i].b.y, c * v.b.y);
         }
       }
-      __syncthreads();
     }
+    __syncthreads();
   }
-  for (int i = tid; i < K; i += nt) Y[i] = cadd(Y[i], Cc[i]);
+  // phase 3: Y (aliasing the phase-1 arrays) = sum + compensation
+#pragma unroll
+  for (int i = 0; i < BINS_PER_THREAD; ++i) Y[tid + i * nt] = eadd(acc[i], cmp[i]);
   __syncthreads();
   fft_smem<-1, T>(Y, 1, 0, tid, K, sc.logK, A.tab.tw_K, true);
-  C* out = A.out + size_t(col) * nz;
+  C* o1 = A.out + size_t(c1) * nz;
+  C* o2 = A.out + size_t(c2) * nz;
   for (int n = tid; n < nz; n += nt) {
     int p = n - nz / 2;
     if (p < 0) p += K;
-    out[n] = cscale(Y[p], __ldg(A.tab.scale + n));
+    const T s = __ldg(A.tab.scale + n);
+    const V y = Y[p];
+    o1[n] = cscale(y.a, s);
+    if (two) o2[n] = cscale(y.b, s);
   }
 }
 
-template <typename T>
-static size_t ax_smem(int K, int J, bool adj) {
-  return size_t(K) * sizeof(cplx<T>) * (adj ? 2 : 1) + size_t(TABLE_D + 1) * 2 * J * sizeof(T);
+template <typename T> size_t ax_smem_bytes(int K, int nk, bool adj) {
+  const size_t y = size_t(K) * sizeof(cpair<T>);
+  if (!adj) return y;
+  const size_t arrays = size_t(nk) * (sizeof(cpair<T>) + sizeof(T) + sizeof(int)) +
+                        size_t(2 * K) * sizeof(unsigned short);
+  return y > arrays ? y : arrays;
 }
+template size_t ax_smem_bytes<float>(int, int, bool);
+template size_t ax_smem_bytes<double>(int, int, bool);
 
 template <typename T, int J>
-static cudaError_t launch_ax_J(const AxArgs<T>& a, int ncols, cudaStream_t s, bool adj) {
+static cudaError_t launch_ax_J(const AxArgs<T>& a, int npairs, cudaStream_t s, bool adj) {
   const int K = a.sc.K;
   const int threads = K / 8;
-  const size_t sm = ax_smem<T>(K, J, adj);
+  const size_t sm = ax_smem_bytes<T>(K, a.sc.nk, adj);
   if (adj) {
     cudaFuncSetAttribute(k_ax_adj<T, J>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-    k_ax_adj<T, J><<<ncols, threads, sm, s>>>(a);
+    k_ax_adj<T, J><<<npairs, threads, sm, s>>>(a);
   } else {
     cudaFuncSetAttribute(k_ax_fwd<T, J>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-    k_ax_fwd<T, J><<<ncols, threads, sm, s>>>(a);
+    k_ax_fwd<T, J><<<npairs, threads, sm, s>>>(a);
   }
   return cudaGetLastError();
 }
 
 template <typename T>
-static cudaError_t launch_ax(const AxArgs<T>& a, int ncols, cudaStream_t s, bool adj) {
+static cudaError_t launch_ax(const AxArgs<T>& a, int npairs, cudaStream_t s, bool adj) {
   switch (a.sc.J) {
-    case 4: return launch_ax_J<T, 4>(a, ncols, s, adj);
-    case 6: return launch_ax_J<T, 6>(a, ncols, s, adj);
-    case 8: return launch_ax_J<T, 8>(a, ncols, s, adj);
+    case 4: return launch_ax_J<T, 4>(a, npairs, s, adj);
+    case 6: return launch_ax_J<T, 6>(a, npairs, s, adj);
+    case 8: return launch_ax_J<T, 8>(a, npairs, s, adj);
   }
   return cudaErrorInvalidValue;
 }
 
-template <typename T> cudaError_t launch_ax_fwd(const AxArgs<T>& a, int ncols, cudaStream_t s) {
-  return launch_ax<T>(a, ncols, s, false);
+template <typename T> cudaError_t launch_ax_fwd(const AxArgs<T>& a, int npairs, cudaStream_t s) {
+  return launch_ax<T>(a, npairs, s, false);
 }
-template <typename T> cudaError_t launch_ax_adj(const AxArgs<T>& a, int ncols, cudaStream_t s) {
-  return launch_ax<T>(a, ncols, s, true);
+template <typename T> cudaError_t launch_ax_adj(const AxArgs<T>& a, int npairs, cudaStream_t s) {
+  return launch_ax<T>(a, npairs, s, true);
 }
 
 template cudaError_t launch_ax_fwd<float>(const AxArgs<float>&, int, cudaStream_t);

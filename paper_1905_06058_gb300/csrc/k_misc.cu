@@ -9,7 +9,7 @@
 //   r_l(f)   = sum_{n'} s(n') cos(g (f - 1/2 - lam_l) n'),
 // s(n') = psi_hat(0) / psi_hat(n'/K), psi_hat the Kaiser-Bessel transform
 // with alpha = 2.34 J.  These sums and the J x J Cholesky solves run in FP64
-// on the device (cond(G) < 1e5 for J <= 8), one block per table node.
+// on the device (cond(G) < 1e5 for J <= 8), one block per offset.
 #include <math.h>
 
 #include "internal.cuh"
@@ -37,12 +37,13 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return t;   // valid in thread 0
 }
 
-// grid: TABLE_D + 1 blocks of 256 threads; out64[i*J + l] = c_l(i / TABLE_D)
-__global__ void __launch_bounds__(256) k_minmax_nodes(int nz, int K, int J, double* out64) {
+// one block of 256 threads per offset f[i]; out64[i*J + l] = c_l(f[i])
+__global__ void __launch_bounds__(256) k_minmax_nodes(int nz, int K, int J, const double* fs,
+                                                      double* out64) {
   __shared__ double red[8];
   __shared__ double gsum[8], rsum[8];
   const double g = 2.0 * M_PI / K;
-  const double f = double(blockIdx.x) / double(TABLE_D);
+  const double f = fs[blockIdx.x];
   double pg[8], pr[8];
   for (int d = 0; d < 8; ++d) { pg[d] = 0.0; pr[d] = 0.0; }
   for (int n = -nz / 2 + int(threadIdx.x); n <= nz / 2; n += blockDim.x) {
@@ -83,31 +84,11 @@ __global__ void __launch_bounds__(256) k_minmax_nodes(int nz, int K, int J, doub
   }
 }
 
-// Pack as rows [c_0..c_{J-1}, c(next) - c(this)] in type T.
-template <typename T>
-__global__ void k_minmax_pack(const double* in64, int J, T* out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i > TABLE_D) return;
-  for (int l = 0; l < J; ++l) {
-    const double c = in64[i * J + l];
-    const double cn = i < TABLE_D ? in64[(i + 1) * J + l] : c;
-    out[i * 2 * J + l] = T(c);
-    out[i * 2 * J + J + l] = T(cn - c);
-  }
+cudaError_t minmax_nodes(int nz, int K, int J, const double* f, int n, double* out,
+                         cudaStream_t s) {
+  k_minmax_nodes<<<n, 256, 0, s>>>(nz, K, J, f, out);
+  return cudaGetLastError();
 }
-
-template <typename T> cudaError_t build_minmax_table(int nz, int K, int J, T* out, cudaStream_t s) {
-  double* tmp = nullptr;
-  cudaError_t e = cudaMallocAsync(&tmp, sizeof(double) * (TABLE_D + 1) * J, s);
-  if (e != cudaSuccess) return e;
-  k_minmax_nodes<<<TABLE_D + 1, 256, 0, s>>>(nz, K, J, tmp);
-  k_minmax_pack<T><<<(TABLE_D + 1 + 255) / 256, 256, 0, s>>>(tmp, J, out);
-  e = cudaGetLastError();
-  cudaFreeAsync(tmp, s);
-  return e;
-}
-template cudaError_t build_minmax_table<float>(int, int, int, float*, cudaStream_t);
-template cudaError_t build_minmax_table<double>(int, int, int, double*, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // Reductions: stage 1 writes one partial per block, stage 2 combines them in a

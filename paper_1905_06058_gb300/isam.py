@@ -245,7 +245,9 @@ class Plan:
         return dict(iterations=info.iterations, rr=info.rr, lam=info.lambda_, L=info.L,
                     status=info.status)
 
-    def lipschitz(self, iters=100, rtol=1e-9, v0=None) -> float:
+    def lipschitz(self, iters=0, rtol=0.0, v0=None) -> float:
+        """L = ||A^H A|| by power iteration; iters = 0 uses the library default
+        (the estimate isam_solve caches when no L is given)."""
         self._sync_stream()
         L = ctypes.c_double()
         p = None if v0 is None else self._dev(v0, self.cplx_dtype, self.image_shape, "v0")
