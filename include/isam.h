@@ -152,7 +152,7 @@ int64_t isam_last_launch_count(const isam_plan* plan);
 enum {
   ISAM_KCLASS_AX_FWD = 0,      /* Stolt NUFFT forward (axial)               */
   ISAM_KCLASS_AX_ADJ = 1,      /* Stolt NUFFT adjoint (axial)               */
-  ISAM_KCLASS_LAT_MID = 2,     /* fused lateral IFFT, Re, -s_d, FFT         */
+  ISAM_KCLASS_AX_FUSED = 2,    /* Stolt NUFFT, residual, adjoint NUFFT      */
   ISAM_KCLASS_LAT_UPDATE = 3,  /* fused lateral IFFT, FISTA step, FFT       */
   ISAM_KCLASS_LAT_FFT = 4,     /* plain lateral FFT passes                  */
   ISAM_KCLASS_MISC = 5,        /* reductions and elementwise kernels        */

@@ -9,9 +9,8 @@
 // 16- or 32-byte shared-memory access per point).
 //
 // Direction SIGN = -1 computes X_m = sum_p x_p e^{-2 pi i m p / L},
-// SIGN = +1 the same with e^{+...}; no normalisation.  Twiddles come from a
-// table tw[m] = e^{-2 pi i m / L}, m < L (FP64-rounded), read through the
-// read-only cache; SIGN = +1 conjugates them.
+// SIGN = +1 the same with e^{+...}; no normalisation.  Twiddles are computed
+// per butterfly: one sincospi of the exact rational angle, then powers.
 #pragma once
 
 #include "common.cuh"
@@ -89,20 +88,40 @@ __device__ __forceinline__ void dft8(E* a) {
   a[3] = eadd(e3, p3); a[7] = esub(e3, p3);
 }
 
-template <int SIGN, typename T>
-__device__ __forceinline__ cplx<T> twiddle(const cplx<T>* __restrict__ tw, int m) {
-  cplx<T> w = __ldg(tw + m);
-  if (SIGN > 0) w.y = -w.y;
-  return w;
+// Shared-memory row of logical row r: one padding row after every 8 rows,
+// which makes the strided Stockham writes of 8- and 16-byte elements free of
+// bank conflicts.  A column of L rows occupies padded_rows(L) rows.
+__host__ __device__ __forceinline__ int prow(int r) { return r + (r >> 3); }
+__host__ __device__ __forceinline__ int padded_rows(int L) { return L + (L >> 3); }
+
+__device__ __forceinline__ void sincospi_(float x, float* s, float* c) { sincospif(x, s, c); }
+__device__ __forceinline__ void sincospi_(double x, double* s, double* c) { sincospi(x, s, c); }
+
+// w[r] = e^{SIGN 2 pi i r k / N} for r = 1..R-1: one sincospi, then powers.
+template <int SIGN, int R, typename T>
+__device__ __forceinline__ void twiddles(int k, int N, cplx<T>* w) {
+  T s, c;
+  sincospi_(T(2 * k) / T(N), &s, &c);
+  w[1] = mk<T>(c, SIGN * s);
+  if (R >= 4) {
+    w[2] = cmul(w[1], w[1]);
+    w[3] = cmul(w[2], w[1]);
+  }
+  if (R == 8) {
+    w[4] = cmul(w[2], w[2]);
+    w[5] = cmul(w[4], w[1]);
+    w[6] = cmul(w[3], w[3]);
+    w[7] = cmul(w[4], w[3]);
+  }
 }
 
-// One Stockham pass of radix R on column `col` (element r at buf[r*stride+col]);
-// this thread does 8/R butterflies j = b + u * (L/8).  Reads all its inputs,
-// block barrier, writes.  Must be reached by every thread of the block.
+// One Stockham pass of radix R on column `col` (logical row r at
+// buf[prow(r)*stride+col]); this thread does 8/R butterflies j = b + u * (L/8).
+// Reads all its inputs, block barrier, writes.  Every thread of the block
+// must reach it.
 template <int SIGN, int R, typename T, typename E>
 __device__ __forceinline__ void stockham_pass(E* buf, int stride, int col, int b, int L,
-                                              int Ns, const cplx<T>* __restrict__ tw,
-                                              bool active) {
+                                              int Ns, bool active) {
   constexpr int NB = 8 / R;          // butterflies per thread
   const int LR = L / R;
   const int L8 = L >> 3;
@@ -112,7 +131,7 @@ __device__ __forceinline__ void stockham_pass(E* buf, int stride, int col, int b
     for (int u = 0; u < NB; ++u) {
       const int j = b + u * L8;
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[u * R + r] = buf[(j + r * LR) * stride + col];
+      for (int r = 0; r < R; ++r) v[u * R + r] = buf[prow(j + r * LR) * stride + col];
     }
   }
   __syncthreads();
@@ -123,16 +142,17 @@ __device__ __forceinline__ void stockham_pass(E* buf, int stride, int col, int b
       const int k = j & (Ns - 1);
       E* a = v + u * R;
       if (Ns > 1) {
-        const int step = (L / (Ns * R)) * k;   // twiddle index for r = 1
+        cplx<T> w[8];
+        twiddles<SIGN, R, T>(k, Ns * R, w);
 #pragma unroll
-        for (int r = 1; r < R; ++r) a[r] = emul(a[r], twiddle<SIGN, T>(tw, r * step));
+        for (int r = 1; r < R; ++r) a[r] = emul(a[r], w[r]);
       }
       if (R == 8) dft8<SIGN>(a);
       else if (R == 4) dft4<SIGN>(a[0], a[1], a[2], a[3]);
       else dft2<SIGN>(a[0], a[1]);
       const int base = (j - k) * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) buf[(base + r * Ns) * stride + col] = a[r];
+      for (int r = 0; r < R; ++r) buf[prow(base + r * Ns) * stride + col] = a[r];
     }
   }
   __syncthreads();
@@ -144,17 +164,17 @@ __device__ __forceinline__ void stockham_pass(E* buf, int stride, int col, int b
 // it (it contains barriers); it ends with a barrier.
 template <int SIGN, typename T, typename E>
 __device__ __forceinline__ void fft_smem(E* buf, int stride, int col, int b, int L, int logL,
-                                         const cplx<T>* __restrict__ tw, bool active) {
+                                         bool active) {
   if (L >= 8) {
     int Ns = 1;
     const int n8 = logL / 3;
     for (int p = 0; p < n8; ++p) {
-      stockham_pass<SIGN, 8, T>(buf, stride, col, b, L, Ns, tw, active);
+      stockham_pass<SIGN, 8, T>(buf, stride, col, b, L, Ns, active);
       Ns *= 8;
     }
     const int rem = logL - 3 * n8;
-    if (rem == 2) stockham_pass<SIGN, 4, T>(buf, stride, col, b, L, Ns, tw, active);
-    else if (rem == 1) stockham_pass<SIGN, 2, T>(buf, stride, col, b, L, Ns, tw, active);
+    if (rem == 2) stockham_pass<SIGN, 4, T>(buf, stride, col, b, L, Ns, active);
+    else if (rem == 1) stockham_pass<SIGN, 2, T>(buf, stride, col, b, L, Ns, active);
   } else {
     __syncthreads();
     if (active && b == 0 && L > 1) {

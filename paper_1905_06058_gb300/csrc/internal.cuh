@@ -28,9 +28,6 @@ struct StoltConst {
 };
 
 template <typename T> struct Tables {
-  cplx<T>* tw_x = nullptr;   // [nx]  e^{-2 pi i m / nx}
-  cplx<T>* tw_y = nullptr;   // [ny]
-  cplx<T>* tw_K = nullptr;   // [K]
   T* scale = nullptr;        // [nz]  s(n - nz/2) / sqrt(nz)
   cplx<T>* disp = nullptr;   // [nk]  e^{j phi(k_j)}
 };
@@ -56,7 +53,6 @@ enum LatMode : int {
   LAT_C2C_INV = 1,   // X = F^-1 x
   LAT_R2C_FWD = 2,   // real input, X = F x
   LAT_INV_REAL = 3,  // real output, Re(F^-1 x)
-  LAT_MID = 4,       // R = F( Re(F^-1 S) - s_d )
   LAT_UPDATE = 5,    // FISTA step in image space between F^-1 and F
 };
 
@@ -64,11 +60,8 @@ template <typename T> struct LatArgs {
   const void* in;        // complex (or real for R2C)
   void* out;             // complex (or real for INV_REAL)
   int B, L, logL, M;     // data viewed as [B][L][M], transform along L
-  int TZ, logTZ;         // columns per block
-  const cplx<T>* tw;     // twiddles of length L
+  int TZ, logTZ;         // pair-columns (2 columns each) per block
   T norm;                // 1/sqrt(L)
-  // LAT_MID
-  const T* s_d;          // [B][L][M] real
   // LAT_UPDATE
   const cplx<T>* z1;     // z^{k-1}
   const cplx<T>* z2;     // z^{k-2}
@@ -89,12 +82,17 @@ template <typename T> struct AxArgs {
   Tables<T> tab;
   Poly<T> poly;
   const int2* pairs;
+  // fused kernel only: lateral spectrum of the data, F s_d ([ny][nx][nk]; the
+  // first column of each pair is read), and optional per-block ||R||^2
+  const cplx<T>* sdh;
+  double* partial;
 };
 
 // launchers (return cudaGetLastError())
 template <typename T> cudaError_t launch_lat(int mode, const LatArgs<T>& a, cudaStream_t s);
 template <typename T> cudaError_t launch_ax_fwd(const AxArgs<T>& a, int npairs, cudaStream_t s);
 template <typename T> cudaError_t launch_ax_adj(const AxArgs<T>& a, int npairs, cudaStream_t s);
+template <typename T> cudaError_t launch_ax_fused(const AxArgs<T>& a, int npairs, cudaStream_t s);
 template <typename T> size_t ax_smem_bytes(int K, int nk, bool adj);
 
 // FP64 exact min-max coefficients at offsets f[0..n) (device), out[i*J + l]
@@ -121,6 +119,7 @@ template <typename T> cudaError_t launch_rsub(const T* a, const T* b, T* y, size
 template <typename T> cudaError_t launch_caxpy(const cplx<T>* x, const cplx<T>* v, T alpha,
                                                 cplx<T>* y, size_t n, cudaStream_t s);
 
-int lat_tile(int L, int M);   // columns per block of a lateral pass
+int lat_tile(int L, int M);   // pair-columns per block of a lateral pass
+template <typename T> size_t lat_smem_bytes(int L, int TP);
 
 }  // namespace isam

@@ -4,9 +4,10 @@
 //   lateral FFT (x) -> k_ax_fwd (Stolt NUFFT + phases) -> lateral IFFT + Re;
 // per application of A^H:
 //   lateral FFT of the real spectra -> k_ax_adj -> lateral IFFT;
-// per FISTA iteration (Alg. 1) four:
-//   k_ax_fwd -> LAT_MID (IFFT, Re, - s_d, FFT) -> k_ax_adj -> LAT_UPDATE.
-// Volumes (ny > 1) add separate x passes around the y-axis fused passes.
+// per FISTA iteration (Alg. 1) two:
+//   k_ax_fused (forward NUFFT, residual in the lateral-frequency domain,
+//   adjoint NUFFT) -> LAT_UPDATE (lateral IFFT, FISTA step, lateral FFT).
+// Volumes (ny > 1) add separate x passes around the y-axis update pass.
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -27,6 +28,7 @@ template <typename T> struct Impl {
   cplx<T>* eta_hat = nullptr;   // [ny][nx][nz]  lateral spectrum of the image
   cplx<T>* spec = nullptr;      // [ny][nx][nk]  complex spectra (S, then R_hat)
   cplx<T>* grad = nullptr;      // [ny][nx][nz]  G_hat / image temporaries
+  cplx<T>* sdh = nullptr;       // [ny][nx][nk]  F s_d of the current solve
   cplx<T>* zA = nullptr;        // solver iterates
   cplx<T>* zB = nullptr;
   T* s_tmp = nullptr;           // [ny][nx][nk]  real spectra temporary
@@ -142,23 +144,11 @@ template <typename T> isam_status dalloc(T** p, size_t n) {
 }
 
 template <typename T> void impl_free(Impl<T>& im) {
-  cudaFree(im.tab.tw_x); cudaFree(im.tab.tw_y); cudaFree(im.tab.tw_K);
   cudaFree(im.tab.scale); cudaFree(im.tab.disp);
-  cudaFree(im.eta_hat); cudaFree(im.spec); cudaFree(im.grad);
+  cudaFree(im.eta_hat); cudaFree(im.spec); cudaFree(im.grad); cudaFree(im.sdh);
   cudaFree(im.zA); cudaFree(im.zB); cudaFree(im.s_tmp);
   cudaFree(im.s_host_stage); cudaFree(im.out_stage);
   im = Impl<T>();
-}
-
-// e^{-2 pi i m / L}, m < L, computed in FP64 then rounded to T
-template <typename T> isam_status upload_twiddles(cplx<T>** dst, int L) {
-  std::vector<cplx<T>> h(L);
-  for (int m = 0; m < L; ++m) {
-    const double a = -2.0 * M_PI * double(m) / double(L);
-    h[m] = mk<T>(T(cos(a)), T(sin(a)));
-  }
-  ISAM_TRY(dalloc(dst, L));
-  return from_cuda(cudaMemcpy(*dst, h.data(), sizeof(cplx<T>) * L, cudaMemcpyHostToDevice));
 }
 
 double host_kb_scale(int n, int K, int J) {
@@ -177,9 +167,6 @@ template <typename T> isam_status impl_init(isam_plan* P, Impl<T>& im) {
   if (im.ready) return ISAM_OK;
   if (!precision_fits<T>(P)) return ISAM_ERR_UNSUPPORTED;
   const isam_params& p = P->p;
-  ISAM_TRY(upload_twiddles<T>(&im.tab.tw_x, P->nx));
-  ISAM_TRY(upload_twiddles<T>(&im.tab.tw_y, P->ny));
-  ISAM_TRY(upload_twiddles<T>(&im.tab.tw_K, P->K));
   // scaling s(n - nz/2) / sqrt(nz)
   {
     std::vector<T> h(P->nz);
@@ -219,21 +206,17 @@ template <> Impl<double>& impl_of<double>(isam_plan* P) { return P->f64; }
 // launch helpers
 // ----------------------------------------------------------------------------
 template <typename T>
-LatArgs<T> lat_args(const Impl<T>& im, int B, int L, int M, const cplx<T>* tw, const void* in,
-                    void* out) {
+LatArgs<T> lat_args(int B, int L, int M, const void* in, void* out) {
   LatArgs<T> a{};
   a.in = in; a.out = out;
   a.B = B; a.L = L; a.logL = ilog2(L); a.M = M;
   a.TZ = lat_tile(L, M); a.logTZ = ilog2(a.TZ);
-  a.tw = tw;
   a.norm = T(1.0 / sqrt(double(L)));
-  (void)im;
   return a;
 }
 
 template <typename T> isam_status lat(isam_plan* P, int mode, const LatArgs<T>& a) {
-  const int cls = mode == LAT_MID ? ISAM_KCLASS_LAT_MID
-                : mode == LAT_UPDATE ? ISAM_KCLASS_LAT_UPDATE : ISAM_KCLASS_LAT_FFT;
+  const int cls = mode == LAT_UPDATE ? ISAM_KCLASS_LAT_UPDATE : ISAM_KCLASS_LAT_FFT;
   return launch(P, cls, [&] { return launch_lat<T>(mode, a, P->stream); });
 }
 
@@ -254,18 +237,20 @@ template <typename T> AxArgs<T> ax_args(isam_plan* P, const Impl<T>& im, const c
 template <typename T> isam_status lat_forward(isam_plan* P, Impl<T>& im, const void* in,
                                               cplx<T>* out, int W, bool real_in) {
   const int m0 = real_in ? LAT_R2C_FWD : LAT_C2C_FWD;
-  if (P->ny == 1) return lat<T>(P, m0, lat_args<T>(im, 1, P->nx, W, im.tab.tw_x, in, out));
-  ISAM_TRY(lat<T>(P, m0, lat_args<T>(im, P->ny, P->nx, W, im.tab.tw_x, in, out)));
-  return lat<T>(P, LAT_C2C_FWD, lat_args<T>(im, 1, P->ny, P->nx * W, im.tab.tw_y, out, out));
+  (void)im;
+  if (P->ny == 1) return lat<T>(P, m0, lat_args<T>(1, P->nx, W, in, out));
+  ISAM_TRY(lat<T>(P, m0, lat_args<T>(P->ny, P->nx, W, in, out)));
+  return lat<T>(P, LAT_C2C_FWD, lat_args<T>(1, P->ny, P->nx * W, out, out));
 }
 
 // F_lat^{-1} x, complex or real (Re) output; `in` is overwritten for volumes
 template <typename T> isam_status lat_inverse(isam_plan* P, Impl<T>& im, cplx<T>* in, void* out,
                                               int W, bool real_out) {
   const int m1 = real_out ? LAT_INV_REAL : LAT_C2C_INV;
-  if (P->ny == 1) return lat<T>(P, m1, lat_args<T>(im, 1, P->nx, W, im.tab.tw_x, in, out));
-  ISAM_TRY(lat<T>(P, LAT_C2C_INV, lat_args<T>(im, 1, P->ny, P->nx * W, im.tab.tw_y, in, in)));
-  return lat<T>(P, m1, lat_args<T>(im, P->ny, P->nx, W, im.tab.tw_x, in, out));
+  (void)im;
+  if (P->ny == 1) return lat<T>(P, m1, lat_args<T>(1, P->nx, W, in, out));
+  ISAM_TRY(lat<T>(P, LAT_C2C_INV, lat_args<T>(1, P->ny, P->nx * W, in, in)));
+  return lat<T>(P, m1, lat_args<T>(P->ny, P->nx, W, in, out));
 }
 
 template <typename T> isam_status op_forward(isam_plan* P, const void* eta, void* s) {
@@ -347,35 +332,21 @@ template <typename T> isam_status power_iteration(isam_plan* P, int iters, doubl
 // ----------------------------------------------------------------------------
 // FISTA (Alg. 1)
 // ----------------------------------------------------------------------------
-template <typename T> isam_status fista_iteration(isam_plan* P, Impl<T>& im, const T* s_d,
+template <typename T> isam_status fista_iteration(isam_plan* P, Impl<T>& im,
                                                   const cplx<T>* z1, const cplx<T>* z2,
                                                   cplx<T>* zout, const T* w, double lam,
                                                   double L, double mu_prev, double mu,
                                                   bool norms) {
   cudaStream_t s = P->stream;
-  ISAM_TRY(launch(P, ISAM_KCLASS_AX_FWD, [&] {
-    return launch_ax_fwd<T>(ax_args<T>(P, im, im.eta_hat, im.spec), P->npairs, s);
-  }));
-  if (P->ny == 1) {
-    LatArgs<T> a = lat_args<T>(im, 1, P->nx, P->nk, im.tab.tw_x, im.spec, im.spec);
-    a.s_d = s_d;
-    ISAM_TRY(lat<T>(P, LAT_MID, a));
-  } else {
-    ISAM_TRY(lat<T>(P, LAT_C2C_INV, lat_args<T>(im, P->ny, P->nx, P->nk, im.tab.tw_x, im.spec, im.spec)));
-    LatArgs<T> a = lat_args<T>(im, 1, P->ny, P->nx * P->nk, im.tab.tw_y, im.spec, im.spec);
-    a.s_d = s_d;
-    ISAM_TRY(lat<T>(P, LAT_MID, a));
-    ISAM_TRY(lat<T>(P, LAT_C2C_FWD, lat_args<T>(im, P->ny, P->nx, P->nk, im.tab.tw_x, im.spec, im.spec)));
-  }
-  ISAM_TRY(launch(P, ISAM_KCLASS_AX_ADJ, [&] {
-    return launch_ax_adj<T>(ax_args<T>(P, im, im.spec, im.grad), P->npairs, s);
-  }));
+  AxArgs<T> ax = ax_args<T>(P, im, im.eta_hat, im.grad);
+  ax.sdh = im.sdh;
+  ISAM_TRY(launch(P, ISAM_KCLASS_AX_FUSED, [&] { return launch_ax_fused<T>(ax, P->npairs, s); }));
   LatArgs<T> u;
   if (P->ny == 1) {
-    u = lat_args<T>(im, 1, P->nx, P->nz, im.tab.tw_x, im.grad, im.eta_hat);
+    u = lat_args<T>(1, P->nx, P->nz, im.grad, im.eta_hat);
   } else {
-    ISAM_TRY(lat<T>(P, LAT_C2C_INV, lat_args<T>(im, P->ny, P->nx, P->nz, im.tab.tw_x, im.grad, im.grad)));
-    u = lat_args<T>(im, 1, P->ny, P->nx * P->nz, im.tab.tw_y, im.grad, im.eta_hat);
+    ISAM_TRY(lat<T>(P, LAT_C2C_INV, lat_args<T>(P->ny, P->nx, P->nz, im.grad, im.grad)));
+    u = lat_args<T>(1, P->ny, P->nx * P->nz, im.grad, im.eta_hat);
   }
   u.z1 = z1; u.z2 = z2; u.zout = zout; u.w = w; u.nz = P->nz;
   u.inv_L = T(1.0 / L); u.lam_over_L = T(lam / L); u.mu_prev = T(mu_prev); u.mu = T(mu);
@@ -383,11 +354,11 @@ template <typename T> isam_status fista_iteration(isam_plan* P, Impl<T>& im, con
   u.flag = P->flag;
   ISAM_TRY(lat<T>(P, LAT_UPDATE, u));
   if (norms) {
-    const int nblk = (u.M / u.TZ) * u.B;
+    const int nblk = (u.M / (2 * u.TZ)) * u.B;
     ISAM_TRY(launch(P, ISAM_KCLASS_MISC, [&] { return launch_sum3(P->partial, nblk, P->dscal + 1, s); }));
   }
   if (P->ny > 1)
-    ISAM_TRY(lat<T>(P, LAT_C2C_FWD, lat_args<T>(im, P->ny, P->nx, P->nz, im.tab.tw_x, im.eta_hat, im.eta_hat)));
+    ISAM_TRY(lat<T>(P, LAT_C2C_FWD, lat_args<T>(P->ny, P->nx, P->nz, im.eta_hat, im.eta_hat)));
   return ISAM_OK;
 }
 
@@ -450,6 +421,9 @@ template <typename T> isam_status solve_impl(isam_plan* P, const T* s_d, const i
     CUDA_TRY(cudaMemsetAsync(zQ, 0, sizeof(cplx<T>) * P->n_img, s));
     CUDA_TRY(cudaMemsetAsync(im.eta_hat, 0, sizeof(cplx<T>) * P->n_img, s));
   }
+  // lateral spectrum of the data, used by every iteration's residual
+  if (!im.sdh) ISAM_TRY(dalloc(&im.sdh, P->n_spec));
+  ISAM_TRY(lat_forward<T>(P, im, s_d, im.sdh, P->nk, true));
   const bool check = o->tol > 0;
   const int every = std::max(1, o->check_every);
   const double eps = o->eps > 0 ? o->eps : 1e-30;
@@ -458,7 +432,7 @@ template <typename T> isam_status solve_impl(isam_plan* P, const T* s_d, const i
   for (int it = 1; it <= o->max_iter; ++it) {
     const int k = k0 + it;
     const bool norms = check && (it % every == 0 || it == o->max_iter);
-    ISAM_TRY(fista_iteration<T>(P, im, s_d, zP, zQ, zQ, static_cast<const T*>(o->w_dev), lam, L,
+    ISAM_TRY(fista_iteration<T>(P, im, zP, zQ, zQ, static_cast<const T*>(o->w_dev), lam, L,
                                 mu[k - 1], mu[k], norms));
     std::swap(zP, zQ);   // zP = z^k, zQ = z^{k-1}
     done = it;
@@ -702,7 +676,8 @@ isam_status isam_plan_create(const isam_params* p, void* stream, isam_plan** out
     // partial sums: reductions use RED_BLOCKS, the FISTA update one per block
     const int L = P->ny == 1 ? P->nx : P->ny;
     const int M = P->ny == 1 ? P->nz : P->nx * P->nz;
-    P->n_partial = std::max(RED_BLOCKS, M / lat_tile(L, M));
+    const int npairs_max = P->nx * P->ny / 2 + 4;
+    P->n_partial = std::max(std::max(RED_BLOCKS, M / (2 * lat_tile(L, M))), npairs_max);
   }
   if (st == ISAM_OK) st = dalloc(&P->partial, size_t(P->n_partial) * 3);
   if (st == ISAM_OK) st = dalloc(&P->dscal, 8);

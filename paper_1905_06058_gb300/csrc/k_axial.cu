@@ -154,21 +154,18 @@ __device__ __forceinline__ void pair_columns(const AxArgs<T>& A, int& c1, int& c
   my = signed_freq(c1 / A.sc.nx, A.sc.ny);
 }
 
-template <typename T, int J>
-__global__ void __launch_bounds__(512) k_ax_fwd(const __grid_constant__ AxArgs<T> A) {
+// Y (padded rows) = scaled, zero-padded columns c1 (a) and c2 (b), then the
+// K-point e^{+} DFT.  Ends with a barrier.
+template <typename T>
+__device__ __forceinline__ void load_and_fft(const AxArgs<T>& A, cpair<T>* Y, int c1, int c2,
+                                             bool two) {
   using C = cplx<T>;
   using V = cpair<T>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   const StoltConst& sc = A.sc;
-  const int K = sc.K, nz = sc.nz, nk = sc.nk;
-  V* Y = reinterpret_cast<V*>(smem_raw);
+  const int K = sc.K, nz = sc.nz;
   const int tid = threadIdx.x, nt = blockDim.x;
-  int c1, c2, mx, my;
-  pair_columns(A, c1, c2, mx, my);
-  const bool two = c2 != c1;
-
   const V zero = {mk<T>(0, 0), mk<T>(0, 0)};
-  for (int i = nz / 2 + tid; i < K - nz / 2; i += nt) Y[i] = zero;
+  for (int i = nz / 2 + tid; i < K - nz / 2; i += nt) Y[prow(i)] = zero;
   const C* x1 = A.in + size_t(c1) * nz;
   const C* x2 = A.in + size_t(c2) * nz;
   for (int n = tid; n < nz; n += nt) {
@@ -178,36 +175,26 @@ __global__ void __launch_bounds__(512) k_ax_fwd(const __grid_constant__ AxArgs<T
     V v;
     v.a = cscale(x1[n], s);
     v.b = two ? cscale(x2[n], s) : mk<T>(0, 0);
-    Y[p] = v;
+    Y[prow(p)] = v;
   }
   __syncthreads();
-  fft_smem<+1, T>(Y, 1, 0, tid, K, sc.logK, A.tab.tw_K, true);
+  fft_smem<+1, T>(Y, 1, 0, tid, K, sc.logK, true);
+}
 
-  const StoltPos<T> sp(sc, mx, my);
-  C* o1 = A.out + size_t(c1) * nk;
-  C* o2 = A.out + size_t(c2) * nk;
-  for (int j = tid; j < nk; j += nt) {
-    int mfl;
-    T frac, turn;
-    C a1 = mk<T>(0, 0), a2 = mk<T>(0, 0);
-    if (sp.at(sc, j, mfl, frac, turn)) {
-      T c[J];
-      coefficients<T, J>(A.poly, frac, c);
-      const int m0 = mfl - J / 2 + 1;
+// forward interpolation of both columns at sample j (before the phase)
+template <typename T, int J>
+__device__ __forceinline__ void interp_pair(const cpair<T>* Y, int K, int mfl, const T* c,
+                                            cplx<T>& a1, cplx<T>& a2) {
+  const int m0 = mfl - J / 2 + 1;
+  a1 = mk<T>(0, 0);
+  a2 = mk<T>(0, 0);
 #pragma unroll
-      for (int l = 0; l < J; ++l) {
-        const V y = Y[(m0 + l) & (K - 1)];
-        a1.x = fma(c[l], y.a.x, a1.x);
-        a1.y = fma(c[l], y.a.y, a1.y);
-        a2.x = fma(c[l], y.b.x, a2.x);
-        a2.y = fma(c[l], y.b.y, a2.y);
-      }
-      const C ph = spectral_phase<T>(sc, A.tab.disp, j, turn);
-      a1 = cmul(a1, ph);
-      a2 = cmul(a2, ph);
-    }
-    o1[j] = a1;
-    if (two) o2[j] = a2;
+  for (int l = 0; l < J; ++l) {
+    const cpair<T> y = Y[prow((m0 + l) & (K - 1))];
+    a1.x = fma(c[l], y.a.x, a1.x);
+    a1.y = fma(c[l], y.a.y, a1.y);
+    a2.x = fma(c[l], y.b.x, a2.x);
+    a2.y = fma(c[l], y.b.y, a2.y);
   }
 }
 
@@ -219,8 +206,131 @@ __device__ __forceinline__ void comp_add(T& sum, T& comp, T v) {
   comp += (sum - (s - bb)) + (v - bb);
   sum = s;
 }
+template <typename T>
+__device__ __forceinline__ void comp_add(cpair<T>& s, cpair<T>& c, T w, const cpair<T>& v) {
+  comp_add(s.a.x, c.a.x, w * v.a.x);
+  comp_add(s.a.y, c.a.y, w * v.a.y);
+  comp_add(s.b.x, c.b.x, w * v.b.x);
+  comp_add(s.b.y, c.b.y, w * v.b.y);
+}
 
+constexpr int MAXU = 4;              // samples per thread: nk <= K/2 = 4 * (K/8)
 constexpr int BINS_PER_THREAD = 8;   // K / blockDim
+
+// Shared-memory arrays of the adjoint gather, aliasing the FFT buffer.
+template <typename T> struct GatherSmem {
+  cpair<T>* val;            // [nk]  conj(phase) R of both columns
+  T* fr;                    // [nk]  fractional Stolt offset
+  int* m0s;                 // [nk]  first neighbour bin (INT_MIN: evanescent)
+  unsigned short* first;    // [2K]  smallest j reaching a bin of the window
+};
+template <typename T>
+__device__ __forceinline__ GatherSmem<T> gather_smem(unsigned char* raw, int nk) {
+  GatherSmem<T> g;
+  g.val = reinterpret_cast<cpair<T>*>(raw);
+  g.fr = reinterpret_cast<T*>(g.val + nk);
+  g.m0s = reinterpret_cast<int*>(g.fr + nk);
+  g.first = reinterpret_cast<unsigned short*>(g.m0s + nk);
+  return g;
+}
+
+// Adjoint interpolation in gather form: after the per-sample arrays are in
+// shared memory, each thread sums the contributions to its bins
+// m = tid + i * blockDim (i < BINS_PER_THREAD) into compensated registers,
+// then (after a barrier) writes Y[prow(m)] -- Y may alias the arrays.
+template <typename T, int J>
+__device__ __forceinline__ void gather_bins(const AxArgs<T>& A, const GatherSmem<T>& g,
+                                            cpair<T>* Y, int ulo, int uhi) {
+  using V = cpair<T>;
+  const int K = A.sc.K, nk = A.sc.nk;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  V acc[BINS_PER_THREAD], cmp[BINS_PER_THREAD];
+#pragma unroll
+  for (int i = 0; i < BINS_PER_THREAD; ++i) {
+    acc[i] = {mk<T>(0, 0), mk<T>(0, 0)};
+    cmp[i] = acc[i];
+  }
+  // windows of 2K unwrapped bins (a single window unless near the cut-off)
+  for (int W0 = ulo; W0 <= uhi; W0 += 2 * K) {
+    const int W1 = min(uhi, W0 + 2 * K - 1);
+    // first[u - W0] = smallest j whose neighbourhood m0_j .. m0_j + J - 1 reaches u
+    for (int j = tid; j < nk; j += nt) {
+      const int m0 = g.m0s[j];
+      if (m0 == INT_MIN) continue;
+      const int prev = (j > 0 && g.m0s[j - 1] != INT_MIN) ? g.m0s[j - 1] + J : INT_MIN;
+      const int a = max(max(prev, ulo), W0);
+      const int b = min(m0 + J - 1, W1);
+      for (int u = a; u <= b; ++u) g.first[u - W0] = (unsigned short)j;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < BINS_PER_THREAD; ++i) {
+      const int m = tid + i * nt;
+      for (int u = W0 + ((m - W0) & (K - 1)); u <= W1; u += K) {
+        for (int j = g.first[u - W0]; j < nk; ++j) {
+          const int m0 = g.m0s[j];
+          if (m0 > u) break;
+          comp_add(acc[i], cmp[i], coefficient<T, J>(A.poly, g.fr[j], u - m0), g.val[j]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < BINS_PER_THREAD; ++i) Y[prow(tid + i * nt)] = eadd(acc[i], cmp[i]);
+  __syncthreads();
+}
+
+// Y (after the e^{-} DFT): truncate to the nz samples, scale, store columns.
+template <typename T>
+__device__ __forceinline__ void store_columns(const AxArgs<T>& A, const cpair<T>* Y, int c1,
+                                              int c2, bool two) {
+  using C = cplx<T>;
+  const int K = A.sc.K, nz = A.sc.nz;
+  C* o1 = A.out + size_t(c1) * nz;
+  C* o2 = A.out + size_t(c2) * nz;
+  for (int n = threadIdx.x; n < nz; n += blockDim.x) {
+    int p = n - nz / 2;
+    if (p < 0) p += K;
+    const T s = __ldg(A.tab.scale + n);
+    const cpair<T> y = Y[prow(p)];
+    o1[n] = cscale(y.a, s);
+    if (two) o2[n] = cscale(y.b, s);
+  }
+}
+
+template <typename T, int J>
+__global__ void __launch_bounds__(512) k_ax_fwd(const __grid_constant__ AxArgs<T> A) {
+  using C = cplx<T>;
+  using V = cpair<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const StoltConst& sc = A.sc;
+  const int K = sc.K, nk = sc.nk;
+  V* Y = reinterpret_cast<V*>(smem_raw);
+  int c1, c2, mx, my;
+  pair_columns(A, c1, c2, mx, my);
+  const bool two = c2 != c1;
+  load_and_fft(A, Y, c1, c2, two);
+
+  const StoltPos<T> sp(sc, mx, my);
+  C* o1 = A.out + size_t(c1) * nk;
+  C* o2 = A.out + size_t(c2) * nk;
+  for (int j = threadIdx.x; j < nk; j += blockDim.x) {
+    int mfl;
+    T frac, turn;
+    C a1 = mk<T>(0, 0), a2 = mk<T>(0, 0);
+    if (sp.at(sc, j, mfl, frac, turn)) {
+      T c[J];
+      coefficients<T, J>(A.poly, frac, c);
+      interp_pair<T, J>(Y, K, mfl, c, a1, a2);
+      const C ph = spectral_phase<T>(sc, A.tab.disp, j, turn);
+      a1 = cmul(a1, ph);
+      a2 = cmul(a2, ph);
+    }
+    o1[j] = a1;
+    if (two) o2[j] = a2;
+  }
+}
 
 template <typename T, int J>
 __global__ void __launch_bounds__(512) k_ax_adj(const __grid_constant__ AxArgs<T> A) {
@@ -228,29 +338,23 @@ __global__ void __launch_bounds__(512) k_ax_adj(const __grid_constant__ AxArgs<T
   using V = cpair<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const StoltConst& sc = A.sc;
-  const int K = sc.K, nz = sc.nz, nk = sc.nk;
-  // phase 1 arrays (aliased by Y in phase 3)
-  V* val = reinterpret_cast<V*>(smem_raw);                  // [nk]
-  T* fr = reinterpret_cast<T*>(val + nk);                   // [nk]
-  int* m0s = reinterpret_cast<int*>(fr + nk);               // [nk]
-  unsigned short* first = reinterpret_cast<unsigned short*>(m0s + nk);   // [2K]
-  V* Y = reinterpret_cast<V*>(smem_raw);                    // [K]
+  const int nk = sc.nk;
+  const GatherSmem<T> g = gather_smem<T>(smem_raw, nk);
+  V* Y = reinterpret_cast<V*>(smem_raw);
   __shared__ int u_lo, u_hi;
   const int tid = threadIdx.x, nt = blockDim.x;
   int c1, c2, mx, my;
   pair_columns(A, c1, c2, mx, my);
   const bool two = c2 != c1;
-
   if (tid == 0) { u_lo = INT_MAX; u_hi = INT_MIN; }
   __syncthreads();
-  // phase 1: per sample j, position, coefficient offset and phased values
   const StoltPos<T> sp(sc, mx, my);
   const C* r1 = A.in + size_t(c1) * nk;
   const C* r2 = A.in + size_t(c2) * nk;
-  int my_lo = INT_MAX, my_hi = INT_MIN;
+  int lo = INT_MAX, hi = INT_MIN;
   for (int j = tid; j < nk; j += nt) {
     int mfl;
-    T frac, turn;
+    T frac = T(0), turn;
     V v = {mk<T>(0, 0), mk<T>(0, 0)};
     int m0 = INT_MIN;
     if (sp.at(sc, j, mfl, frac, turn)) {
@@ -258,77 +362,121 @@ __global__ void __launch_bounds__(512) k_ax_adj(const __grid_constant__ AxArgs<T
       v.a = cmulc(r1[j], ph);
       v.b = two ? cmulc(r2[j], ph) : mk<T>(0, 0);
       m0 = mfl - J / 2 + 1;
-      my_lo = min(my_lo, m0);
-      my_hi = max(my_hi, m0);
+      lo = min(lo, m0);
+      hi = max(hi, m0);
     }
-    val[j] = v;
-    fr[j] = frac;
-    m0s[j] = m0;
+    g.val[j] = v;
+    g.fr[j] = frac;
+    g.m0s[j] = m0;
   }
-  if (my_lo != INT_MAX) {
-    atomicMin(&u_lo, my_lo);
-    atomicMax(&u_hi, my_hi + J - 1);
+  if (lo != INT_MAX) {
+    atomicMin(&u_lo, lo);
+    atomicMax(&u_hi, hi + J - 1);
   }
   __syncthreads();
-  const int ulo = u_lo, uhi = u_hi;
-  // per-thread compensated accumulators for bins m = tid + i * nt
-  V acc[BINS_PER_THREAD], cmp[BINS_PER_THREAD];
+  gather_bins<T, J>(A, g, Y, u_lo, u_hi);
+  fft_smem<-1, T>(Y, 1, 0, tid, sc.K, sc.logK, true);
+  store_columns(A, Y, c1, c2, two);
+}
+
+// Forward model, data residual and adjoint of one column pair in one pass
+// (Alg. 1 gradient):  S = phase . N(eta_hat);  the lateral spectrum of the
+// real residual Re(F^{-1} S) - s_d is, column by column,
+//   R(q) = (S(q) + conj(S(-q))) / 2 - F s_d (q),
+// because F(Re v)(q) = (F v(q) + conj(F v(-q))) / 2 and q, -q are the two
+// columns of the pair; then G = N'(conj(phase) R).  F s_d is Hermitian, so
+// only its c1 column is read.  Optionally writes ||R||^2 of the pair.
+template <typename T, int J>
+__global__ void __launch_bounds__(512) k_ax_fused(const __grid_constant__ AxArgs<T> A) {
+  using C = cplx<T>;
+  using V = cpair<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const StoltConst& sc = A.sc;
+  const int K = sc.K, nk = sc.nk;
+  V* Y = reinterpret_cast<V*>(smem_raw);
+  const GatherSmem<T> g = gather_smem<T>(smem_raw, nk);
+  __shared__ int u_lo, u_hi;
+  __shared__ double red[16];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  int c1, c2, mx, my;
+  pair_columns(A, c1, c2, mx, my);
+  const bool two = c2 != c1;
+  if (tid == 0) { u_lo = INT_MAX; u_hi = INT_MIN; }
+  load_and_fft(A, Y, c1, c2, two);
+
+  const StoltPos<T> sp(sc, mx, my);
+  const C* d1 = A.sdh + size_t(c1) * nk;
+  V vals[MAXU];
+  T frs[MAXU];
+  int m0v[MAXU];
+  int lo = INT_MAX, hi = INT_MIN;
+  double rr = 0.0;
 #pragma unroll
-  for (int i = 0; i < BINS_PER_THREAD; ++i) {
-    acc[i] = {mk<T>(0, 0), mk<T>(0, 0)};
-    cmp[i] = acc[i];
-  }
-  // phase 2: windows of 2K unwrapped bins (one window unless near cut-off)
-  for (int W0 = ulo; W0 <= uhi; W0 += 2 * K) {
-    const int W1 = min(uhi, W0 + 2 * K - 1);
-    // first[u - W0] = smallest j whose neighbourhood m0_j .. m0_j + J - 1 reaches u
-    for (int j = tid; j < nk; j += nt) {
-      const int m0 = m0s[j];
-      if (m0 == INT_MIN) continue;
-      const int prev = (j > 0 && m0s[j - 1] != INT_MIN) ? m0s[j - 1] + J : INT_MIN;
-      const int a = max(max(prev, ulo), W0);
-      const int b = min(m0 + J - 1, W1);
-      for (int u = a; u <= b; ++u) first[u - W0] = (unsigned short)j;
+  for (int u = 0; u < MAXU; ++u) {
+    const int j = tid + u * nt;
+    m0v[u] = INT_MIN;
+    frs[u] = T(0);
+    vals[u] = {mk<T>(0, 0), mk<T>(0, 0)};
+    if (j >= nk) continue;
+    const C dq = d1[j];
+    const C dm = cconj(dq);            // F s_d at -q
+    int mfl;
+    T frac, turn;
+    C s1 = mk<T>(0, 0), s2 = mk<T>(0, 0), ph = mk<T>(0, 0);
+    const bool prop = sp.at(sc, j, mfl, frac, turn);
+    if (prop) {
+      T c[J];
+      coefficients<T, J>(A.poly, frac, c);
+      interp_pair<T, J>(Y, K, mfl, c, s1, s2);
+      ph = spectral_phase<T>(sc, A.tab.disp, j, turn);
+      s1 = cmul(s1, ph);
+      s2 = two ? cmul(s2, ph) : s1;
     }
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < BINS_PER_THREAD; ++i) {
-      const int m = tid + i * nt;
-      int u = W0 + ((m - W0) % K + K) % K;
-      for (; u <= W1; u += K) {
-        for (int j = first[u - W0]; j < nk; ++j) {
-          const int m0 = m0s[j];
-          if (m0 > u) break;
-          const T c = coefficient<T, J>(A.poly, fr[j], u - m0);
-          const V v = val[j];
-          comp_add(acc[i].a.x, cmp[i].a.x, c * v.a.x);
-          comp_add(acc[i].a.y, cmp[i].a.y, c * v.a.y);
-          comp_add(acc[i].b.x, cmp[i].b.x, c * v.b.x);
-          comp_add(acc[i].b.y, cmp[i].b.y, c * v.b.y);
-        }
-      }
+    const C R1 = csub(cscale(cadd(s1, cconj(s2)), T(0.5)), dq);
+    const C R2 = csub(cscale(cadd(s2, cconj(s1)), T(0.5)), dm);
+    if (A.partial) {
+      rr += double(R1.x) * R1.x + double(R1.y) * R1.y;
+      if (two) rr += double(R2.x) * R2.x + double(R2.y) * R2.y;
     }
-    __syncthreads();
+    if (prop) {
+      vals[u].a = cmulc(R1, ph);
+      vals[u].b = two ? cmulc(R2, ph) : mk<T>(0, 0);
+      frs[u] = frac;
+      m0v[u] = mfl - J / 2 + 1;
+      lo = min(lo, m0v[u]);
+      hi = max(hi, m0v[u]);
+    }
   }
-  // phase 3: Y (aliasing the phase-1 arrays) = sum + compensation
+  __syncthreads();                       // all reads of Y are done: arrays alias it
 #pragma unroll
-  for (int i = 0; i < BINS_PER_THREAD; ++i) Y[tid + i * nt] = eadd(acc[i], cmp[i]);
+  for (int u = 0; u < MAXU; ++u) {
+    const int j = tid + u * nt;
+    if (j >= nk) continue;
+    g.val[j] = vals[u];
+    g.fr[j] = frs[u];
+    g.m0s[j] = m0v[u];
+  }
+  if (lo != INT_MAX) {
+    atomicMin(&u_lo, lo);
+    atomicMax(&u_hi, hi + J - 1);
+  }
+  if (A.partial) {
+    for (int o = 16; o > 0; o >>= 1) rr += __shfl_xor_sync(0xffffffffu, rr, o);
+    if ((tid & 31) == 0) red[tid >> 5] = rr;
+  }
   __syncthreads();
-  fft_smem<-1, T>(Y, 1, 0, tid, K, sc.logK, A.tab.tw_K, true);
-  C* o1 = A.out + size_t(c1) * nz;
-  C* o2 = A.out + size_t(c2) * nz;
-  for (int n = tid; n < nz; n += nt) {
-    int p = n - nz / 2;
-    if (p < 0) p += K;
-    const T s = __ldg(A.tab.scale + n);
-    const V y = Y[p];
-    o1[n] = cscale(y.a, s);
-    if (two) o2[n] = cscale(y.b, s);
+  if (A.partial && tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (nt >> 5); ++w) t += red[w];
+    A.partial[blockIdx.x] = t;
   }
+  gather_bins<T, J>(A, g, Y, u_lo, u_hi);
+  fft_smem<-1, T>(Y, 1, 0, tid, K, sc.logK, true);
+  store_columns(A, Y, c1, c2, two);
 }
 
 template <typename T> size_t ax_smem_bytes(int K, int nk, bool adj) {
-  const size_t y = size_t(K) * sizeof(cpair<T>);
+  const size_t y = size_t(padded_rows(K)) * sizeof(cpair<T>);
   if (!adj) return y;
   const size_t arrays = size_t(nk) * (sizeof(cpair<T>) + sizeof(T) + sizeof(int)) +
                         size_t(2 * K) * sizeof(unsigned short);
@@ -337,41 +485,52 @@ template <typename T> size_t ax_smem_bytes(int K, int nk, bool adj) {
 template size_t ax_smem_bytes<float>(int, int, bool);
 template size_t ax_smem_bytes<double>(int, int, bool);
 
+enum { AX_FWD = 0, AX_ADJ = 1, AX_FUSED = 2 };
+
 template <typename T, int J>
-static cudaError_t launch_ax_J(const AxArgs<T>& a, int npairs, cudaStream_t s, bool adj) {
+static cudaError_t launch_ax_J(const AxArgs<T>& a, int npairs, cudaStream_t s, int kind) {
   const int K = a.sc.K;
   const int threads = K / 8;
-  const size_t sm = ax_smem_bytes<T>(K, a.sc.nk, adj);
-  if (adj) {
+  const size_t sm = ax_smem_bytes<T>(K, a.sc.nk, kind != AX_FWD);
+  if (kind == AX_ADJ) {
     cudaFuncSetAttribute(k_ax_adj<T, J>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
     k_ax_adj<T, J><<<npairs, threads, sm, s>>>(a);
-  } else {
+  } else if (kind == AX_FWD) {
     cudaFuncSetAttribute(k_ax_fwd<T, J>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
     k_ax_fwd<T, J><<<npairs, threads, sm, s>>>(a);
+  } else {
+    cudaFuncSetAttribute(k_ax_fused<T, J>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    k_ax_fused<T, J><<<npairs, threads, sm, s>>>(a);
   }
   return cudaGetLastError();
 }
 
 template <typename T>
-static cudaError_t launch_ax(const AxArgs<T>& a, int npairs, cudaStream_t s, bool adj) {
+static cudaError_t launch_ax(const AxArgs<T>& a, int npairs, cudaStream_t s, int kind) {
   switch (a.sc.J) {
-    case 4: return launch_ax_J<T, 4>(a, npairs, s, adj);
-    case 6: return launch_ax_J<T, 6>(a, npairs, s, adj);
-    case 8: return launch_ax_J<T, 8>(a, npairs, s, adj);
+    case 4: return launch_ax_J<T, 4>(a, npairs, s, kind);
+    case 6: return launch_ax_J<T, 6>(a, npairs, s, kind);
+    case 8: return launch_ax_J<T, 8>(a, npairs, s, kind);
   }
   return cudaErrorInvalidValue;
 }
 
 template <typename T> cudaError_t launch_ax_fwd(const AxArgs<T>& a, int npairs, cudaStream_t s) {
-  return launch_ax<T>(a, npairs, s, false);
+  return launch_ax<T>(a, npairs, s, AX_FWD);
 }
 template <typename T> cudaError_t launch_ax_adj(const AxArgs<T>& a, int npairs, cudaStream_t s) {
-  return launch_ax<T>(a, npairs, s, true);
+  return launch_ax<T>(a, npairs, s, AX_ADJ);
+}
+template <typename T> cudaError_t launch_ax_fused(const AxArgs<T>& a, int npairs,
+                                                  cudaStream_t s) {
+  return launch_ax<T>(a, npairs, s, AX_FUSED);
 }
 
 template cudaError_t launch_ax_fwd<float>(const AxArgs<float>&, int, cudaStream_t);
 template cudaError_t launch_ax_fwd<double>(const AxArgs<double>&, int, cudaStream_t);
 template cudaError_t launch_ax_adj<float>(const AxArgs<float>&, int, cudaStream_t);
 template cudaError_t launch_ax_adj<double>(const AxArgs<double>&, int, cudaStream_t);
+template cudaError_t launch_ax_fused<float>(const AxArgs<float>&, int, cudaStream_t);
+template cudaError_t launch_ax_fused<double>(const AxArgs<double>&, int, cudaStream_t);
 
 }  // namespace isam

@@ -1,17 +1,16 @@
 // Lateral passes: batched shared-memory FFTs along the lateral axis (x, or y
-// for volumes) of data viewed as [B][L][M], a block owning TZ consecutive
-// columns m of one batch b (rows of TZ contiguous elements, coalesced).
-// Unitary transforms (each axis scaled by 1/sqrt(L)), §2, Eq. 16-17.
+// for volumes) of data viewed as [B][L][M], a block owning 2*TP consecutive
+// columns m of one batch b.  Each shared-memory element holds two adjacent
+// columns (16- or 32-byte accesses, one padding row per 8 rows), global rows
+// are read and written as 2*TP*8 contiguous bytes.  Unitary transforms (each
+// axis scaled by 1/sqrt(L)), §2, Eq. 16-17.
 //
-// Fused variants remove whole round trips through HBM:
-//   LAT_MID     R = F( Re(F^{-1} S) - s_d ): forward-model output, data residual
-//               and the start of the adjoint in one pass (Alg. 1, gradient step);
-//   LAT_UPDATE  g = F^{-1} G, then in image space the FISTA step of Alg. 1:
-//               eta^k = z^{k-1} + mu_{k-1}(z^{k-1} - z^{k-2}),
-//               z^k = T_{lambda w / L}(eta^k - g/L)            (Eq. 14),
-//               eta^{k+1} = z^k + mu_k (z^k - z^{k-1}),
-//               partial norms for the relative residual      (Eq. 15),
-//               then eta_hat^{k+1} = F eta^{k+1}.
+// LAT_UPDATE fuses the FISTA step of Alg. 1 between an inverse and a forward
+// lateral transform:  g = F^{-1} G (the gradient A^H(A eta - s_d)),
+//   eta^k = z^{k-1} + mu_{k-1}(z^{k-1} - z^{k-2}),
+//   z^k = T_{lambda w / L}(eta^k - g/L)                            (Eq. 14),
+//   eta^{k+1} = z^k + mu_k (z^k - z^{k-1}),  eta_hat^{k+1} = F eta^{k+1},
+// with partial norms for the relative residual (Eq. 15).
 #include <math.h>
 
 #include "fft_smem.cuh"
@@ -19,22 +18,24 @@
 
 namespace isam {
 
-int lat_tile(int L, int M) {
-  int tz = L >= 8 ? 8192 / L : 16;
-  if (tz > 16) tz = 16;
-  if (tz > M) tz = M;
-  if (tz < 1) tz = 1;
-  return tz;
+int lat_tile(int L, int M) {   // pair-columns per block
+  int tp = L >= 8 ? 4096 / L : 8;
+  if (tp > 8) tp = 8;
+  if (tp > M / 2) tp = M / 2;
+  if (tp < 1) tp = 1;
+  return tp;
 }
 
-template <typename T>
-__device__ __forceinline__ cplx<T> soft_threshold(cplx<T> u, T tau) {
-  // T_tau(u) = u max(|u|-tau,0) / (max(|u|-tau,0) + tau); 0 where 0/0  (Eq. 14)
-  T mag = sqrt(u.x * u.x + u.y * u.y);
-  T m = mag - tau;
-  m = m > T(0) ? m : T(0);
-  T den = m + tau;
-  T f = den > T(0) ? m / den : T(0);
+// T_tau(u) = u max(|u| - tau, 0) / (max(|u| - tau, 0) + tau)  (Eq. 14),
+// evaluated as u max(1 - tau / |u|, 0); 0 where |u| = 0.
+__device__ __forceinline__ float2 soft_threshold(float2 u, float tau) {
+  const float m2 = fmaf(u.x, u.x, u.y * u.y);
+  const float f = m2 > 0.0f ? fmaxf(1.0f - tau * rsqrtf(m2), 0.0f) : 0.0f;
+  return cscale(u, f);
+}
+__device__ __forceinline__ double2 soft_threshold(double2 u, double tau) {
+  const double m2 = fma(u.x, u.x, u.y * u.y);
+  const double f = m2 > 0.0 ? fmax(1.0 - tau / sqrt(m2), 0.0) : 0.0;
   return cscale(u, f);
 }
 
@@ -44,93 +45,110 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-template <typename T, int MODE>
-__global__ void __launch_bounds__(1024) k_lat(LatArgs<T> a) {
-  using C = cplx<T>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int TZ = a.TZ, L = a.L, logTZ = a.logTZ;
-  const int col = tid & (TZ - 1), b = tid >> logTZ;
-  const size_t M = size_t(a.M);
-  const size_t base = size_t(blockIdx.y) * size_t(L) * M + size_t(blockIdx.x) * TZ;
-  const int n_el = L * TZ;
+template <typename T> struct rpair_t;
+template <> struct rpair_t<float> { using type = float2; };
+template <> struct rpair_t<double> { using type = double2; };
 
-  // load the tile
-  if (MODE == LAT_R2C_FWD) {
-    const T* in = static_cast<const T*>(a.in);
-    for (int e = tid; e < n_el; e += nt) {
-      const size_t gi = base + size_t(e >> logTZ) * M + (e & (TZ - 1));
-      buf[e] = mk<T>(in[gi], T(0));
+template <typename T, int MODE>
+__global__ void __launch_bounds__(512) k_lat(const __grid_constant__ LatArgs<T> a) {
+  using C = cplx<T>;
+  using V = cpair<T>;
+  using RP = typename rpair_t<T>::type;   // two adjacent reals
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* buf = reinterpret_cast<V*>(smem_raw);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int TP = a.TZ, L = a.L, logTP = a.logTZ;
+  const int col = tid & (TP - 1), b = tid >> logTP;
+  const size_t M = size_t(a.M);
+  const size_t m_first = size_t(blockIdx.x) * (2 * TP);
+  const size_t base = size_t(blockIdx.y) * size_t(L) * M + m_first;
+  const int n_el = L * TP;
+
+  // load the tile (element e: row e / TP, pair-column e % TP)
+  for (int e = tid; e < n_el; e += nt) {
+    const int row = e >> logTP, c = e & (TP - 1);
+    const size_t gi = base + size_t(row) * M + 2 * c;
+    V v;
+    if (MODE == LAT_R2C_FWD) {
+      const RP r = *reinterpret_cast<const RP*>(static_cast<const T*>(a.in) + gi);
+      v.a = mk<T>(r.x, T(0));
+      v.b = mk<T>(r.y, T(0));
+    } else {
+      v = *reinterpret_cast<const V*>(static_cast<const C*>(a.in) + gi);
     }
-  } else {
-    const C* in = static_cast<const C*>(a.in);
-    for (int e = tid; e < n_el; e += nt) {
-      const size_t gi = base + size_t(e >> logTZ) * M + (e & (TZ - 1));
-      buf[e] = in[gi];
-    }
+    buf[prow(row) * TP + c] = v;
   }
   __syncthreads();
 
   if (MODE == LAT_C2C_FWD || MODE == LAT_R2C_FWD)
-    fft_smem<-1, T>(buf, TZ, col, b, L, a.logL, a.tw, true);
+    fft_smem<-1, T>(buf, TP, col, b, L, a.logL, true);
   else
-    fft_smem<+1, T>(buf, TZ, col, b, L, a.logL, a.tw, true);
+    fft_smem<+1, T>(buf, TP, col, b, L, a.logL, true);
 
   const T nrm = a.norm;
   if (MODE == LAT_C2C_FWD || MODE == LAT_C2C_INV || MODE == LAT_R2C_FWD) {
     C* out = static_cast<C*>(a.out);
     for (int e = tid; e < n_el; e += nt) {
-      const size_t gi = base + size_t(e >> logTZ) * M + (e & (TZ - 1));
-      out[gi] = cscale(buf[e], nrm);
+      const int row = e >> logTP, c = e & (TP - 1);
+      const size_t gi = base + size_t(row) * M + 2 * c;
+      *reinterpret_cast<V*>(out + gi) = escale(buf[prow(row) * TP + c], nrm);
     }
     return;
   }
   if (MODE == LAT_INV_REAL) {
     T* out = static_cast<T*>(a.out);
     for (int e = tid; e < n_el; e += nt) {
-      const size_t gi = base + size_t(e >> logTZ) * M + (e & (TZ - 1));
-      out[gi] = buf[e].x * nrm;
+      const int row = e >> logTP, c = e & (TP - 1);
+      const size_t gi = base + size_t(row) * M + 2 * c;
+      const V v = buf[prow(row) * TP + c];
+      RP r;
+      r.x = v.a.x * nrm;
+      r.y = v.b.x * nrm;
+      *reinterpret_cast<RP*>(out + gi) = r;
     }
     return;
   }
-  if (MODE == LAT_MID) {
-    for (int e = tid; e < n_el; e += nt) {
-      const size_t gi = base + size_t(e >> logTZ) * M + (e & (TZ - 1));
-      buf[e] = mk<T>(buf[e].x * nrm - a.s_d[gi], T(0));
-    }
-  }
+  // LAT_UPDATE
   double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
-  if (MODE == LAT_UPDATE) {
-    bool bad = false;
-    for (int e = tid; e < n_el; e += nt) {
-      const size_t gi = base + size_t(e >> logTZ) * M + (e & (TZ - 1));
-      const int n = int((size_t(blockIdx.x) * TZ + (e & (TZ - 1))) & size_t(a.nz - 1));
-      const C gl = cscale(buf[e], nrm * a.inv_L);          // g^k = (1/L) A^H(A eta - s)
-      const C z1 = a.z1[gi];
-      const C z2 = a.z2[gi];
-      const C eta = cadd(z1, cscale(csub(z1, z2), a.mu_prev));
-      const T tau = a.w ? a.lam_over_L * a.w[n] : a.lam_over_L;
-      const C z = soft_threshold<T>(csub(eta, gl), tau);
-      a.zout[gi] = z;
-      buf[e] = cadd(z, cscale(csub(z, z1), a.mu));
-      const C d = csub(z, eta);
-      const C dg = cadd(d, gl);
-      acc0 += double(d.x) * d.x + double(d.y) * d.y;
-      acc1 += double(gl.x) * gl.x + double(gl.y) * gl.y;
-      acc2 += double(dg.x) * dg.x + double(dg.y) * dg.y;
-      bad |= !(isfinite(z.x) && isfinite(z.y));
+  bool bad = false;
+  const T sg = nrm * a.inv_L;
+  for (int e = tid; e < n_el; e += nt) {
+    const int row = e >> logTP, c = e & (TP - 1);
+    const size_t gi = base + size_t(row) * M + 2 * c;
+    const int n0 = int((m_first + 2 * c) & size_t(a.nz - 1));
+    const V g = escale(buf[prow(row) * TP + c], sg);        // g^k = (1/L) A^H(A eta - s)
+    const V z1 = *reinterpret_cast<const V*>(a.z1 + gi);
+    const V z2 = *reinterpret_cast<const V*>(a.z2 + gi);
+    const V eta = eadd(z1, escale(esub(z1, z2), a.mu_prev));
+    const T tau0 = a.w ? a.lam_over_L * a.w[n0] : a.lam_over_L;
+    const T tau1 = a.w ? a.lam_over_L * a.w[n0 + 1] : a.lam_over_L;
+    V z;
+    z.a = soft_threshold(csub(eta.a, g.a), tau0);
+    z.b = soft_threshold(csub(eta.b, g.b), tau1);
+    *reinterpret_cast<V*>(a.zout + gi) = z;
+    buf[prow(row) * TP + c] = eadd(z, escale(esub(z, z1), a.mu));
+    if (a.partial) {
+      const V d = esub(z, eta);
+      const V dg = eadd(d, g);
+      acc0 += double(d.a.x) * d.a.x + double(d.a.y) * d.a.y + double(d.b.x) * d.b.x +
+              double(d.b.y) * d.b.y;
+      acc1 += double(g.a.x) * g.a.x + double(g.a.y) * g.a.y + double(g.b.x) * g.b.x +
+              double(g.b.y) * g.b.y;
+      acc2 += double(dg.a.x) * dg.a.x + double(dg.a.y) * dg.a.y + double(dg.b.x) * dg.b.x +
+              double(dg.b.y) * dg.b.y;
     }
-    if (bad) atomicOr(a.flag, 1);
+    bad |= !(isfinite(z.a.x) && isfinite(z.a.y) && isfinite(z.b.x) && isfinite(z.b.y));
   }
+  if (bad) atomicOr(a.flag, 1);
   __syncthreads();
-  fft_smem<-1, T>(buf, TZ, col, b, L, a.logL, a.tw, true);
+  fft_smem<-1, T>(buf, TP, col, b, L, a.logL, true);
   C* out = static_cast<C*>(a.out);
   for (int e = tid; e < n_el; e += nt) {
-    const size_t gi = base + size_t(e >> logTZ) * M + (e & (TZ - 1));
-    out[gi] = cscale(buf[e], nrm);
+    const int row = e >> logTP, c = e & (TP - 1);
+    const size_t gi = base + size_t(row) * M + 2 * c;
+    *reinterpret_cast<V*>(out + gi) = escale(buf[prow(row) * TP + c], nrm);
   }
-  if (MODE == LAT_UPDATE && a.partial != nullptr) {
+  if (a.partial != nullptr) {
     __shared__ double red[3][32];
     acc0 = warp_sum(acc0); acc1 = warp_sum(acc1); acc2 = warp_sum(acc2);
     const int wid = tid >> 5, lane = tid & 31;
@@ -152,12 +170,16 @@ __global__ void __launch_bounds__(1024) k_lat(LatArgs<T> a) {
   }
 }
 
+template <typename T> size_t lat_smem_bytes(int L, int TP) {
+  return size_t(padded_rows(L)) * TP * sizeof(cpair<T>);
+}
+
 template <typename T, int MODE>
 static cudaError_t launch_lat_mode(const LatArgs<T>& a, cudaStream_t s) {
   const int threads = (a.L >= 8 ? a.L / 8 : 1) * a.TZ;
-  const size_t sm = size_t(a.L) * a.TZ * sizeof(cplx<T>);
+  const size_t sm = lat_smem_bytes<T>(a.L, a.TZ);
   cudaFuncSetAttribute(k_lat<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-  dim3 grid(a.M / a.TZ, a.B);
+  dim3 grid(a.M / (2 * a.TZ), a.B);
   k_lat<T, MODE><<<grid, threads, sm, s>>>(a);
   return cudaGetLastError();
 }
@@ -168,7 +190,6 @@ template <typename T> cudaError_t launch_lat(int mode, const LatArgs<T>& a, cuda
     case LAT_C2C_INV: return launch_lat_mode<T, LAT_C2C_INV>(a, s);
     case LAT_R2C_FWD: return launch_lat_mode<T, LAT_R2C_FWD>(a, s);
     case LAT_INV_REAL: return launch_lat_mode<T, LAT_INV_REAL>(a, s);
-    case LAT_MID: return launch_lat_mode<T, LAT_MID>(a, s);
     case LAT_UPDATE: return launch_lat_mode<T, LAT_UPDATE>(a, s);
   }
   return cudaErrorInvalidValue;

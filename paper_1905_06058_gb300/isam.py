@@ -154,7 +154,7 @@ class Plan:
     def last_launch_count(self) -> int:
         return int(_lib.isam_last_launch_count(self._h))
 
-    KERNEL_CLASSES = ("ax_fwd", "ax_adj", "lat_mid", "lat_update", "lat_fft", "misc")
+    KERNEL_CLASSES = ("ax_fwd", "ax_adj", "ax_fused", "lat_update", "lat_fft", "misc")
 
     def profile(self, on: bool) -> None:
         """Time every kernel launch of this plan with CUDA events (per class)."""

@@ -189,3 +189,40 @@ def test_full_bscan_first_iterate_sampled(torch):
     z_ref = O.soft_threshold(ahs / L, lam / L)
     assert rel(z[:, rows], z_ref) < 3e-5
     plan.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-3), ("fp64", 1e-6)])
+def test_volume_fista_matches_oracle(torch, prec, tol):
+    """3-D (2-D lateral FFT, Stolt map in q_x, q_y): the fused residual uses the
+    (q, -q) pairing of both lateral axes."""
+    from paper_1905_06058_gb300.isam import Plan
+    wl = I.small_bscan(nx=8, ny=4, nk=32, nz=64, n_points=6, seed=18)
+    ref = O.IsamOracle(wl.geom, "nufft")
+    s = I.add_noise(ref.forward(wl.eta), 25.0, np.random.default_rng(18))
+    L = O.power_iteration(ref.forward, ref.adjoint, I.start_vector(ref.image_shape, 18), 300,
+                          1e-13)
+    lam = O.lambda_from_data(ref.adjoint, s, 0.02)
+    res = O.fista(ref.forward, ref.adjoint, s, lam, L, max_iter=40, shape=ref.image_shape)
+    plan = Plan(wl.geom, precision=prec)
+    dt = np.float64 if prec == "fp64" else np.float32
+    out, info = plan.solve(dev(torch, s, dt), lambda_rel=0.02, L=L, max_iter=40)
+    assert rel(out.cpu().numpy(), res.eta) < tol
+    plan.close()
+
+
+def test_evanescent_geometry_solve(torch):
+    """Pitch far below lambda/2: many columns evanescent, steep Stolt maps near the
+    cut-off (several gather windows)."""
+    from paper_1905_06058_gb300.isam import Plan
+    wl = I.small_bscan(nx=32, nk=64, nz=64, n_points=6, seed=19, dx_scale=0.08)
+    ref = O.IsamOracle(wl.geom, "nufft")
+    assert (~ref.prop).any()
+    s = ref.forward(wl.eta)
+    L = O.power_iteration(ref.forward, ref.adjoint, I.start_vector(ref.image_shape, 19), 300,
+                          1e-13)
+    lam = O.lambda_from_data(ref.adjoint, s, 0.05)
+    res = O.fista(ref.forward, ref.adjoint, s, lam, L, max_iter=30, shape=ref.image_shape)
+    plan = Plan(wl.geom, precision="fp64")
+    out, info = plan.solve(dev(torch, s, np.float64), lambda_abs=lam, L=L, max_iter=30)
+    assert rel(out.cpu().numpy(), res.eta) < 1e-6
+    plan.close()
