@@ -9,14 +9,11 @@
 //                 sum_l c_l(f_j) Y[(m0_j + l) mod K],
 //     Y = K-point e^{+} DFT of the scaled, zero-padded column
 //         s(n - nz/2) eta_hat(q, z_n) / sqrt(nz) placed at (n - nz/2) mod K.
-//   k_ax_adj  (Eq. 17, the exact adjoint of k_ax_fwd), in gather form: every
-//     oversampled bin u sums c_{u - m0_j}(f_j) conj(phase_j) R_hat(q, k_j) over
-//     the few samples j whose J-neighbourhood covers u (no atomics).  The
-//     contributors of u are found through first[u], the smallest j whose
-//     neighbourhood reaches u, built from the monotone Stolt positions
-//     (dp/dj = 4 kappa / p >= 2 bins per sample).  Each bin is owned by one
-//     thread and accumulated with compensated (TwoSum) summation in
-//     registers; then the K-point e^{-} DFT, truncation and scaling.
+//   k_ax_adj  (Eq. 17, the exact adjoint of k_ax_fwd): every sample adds
+//     c_l(f_j) conj(phase_j) R_hat(q, k_j) to bins m0_j + l, race-free without
+//     atomics (see scatter_samples), then the K-point e^{-} DFT, truncation
+//     and scaling.
+//   k_ax_fused  both, with the data residual formed in between.
 //
 // Stolt positions are evaluated per sample from per-plan constants in
 // float-float arithmetic (FP32 path) or double (FP64 path): the grid
@@ -198,86 +195,78 @@ __device__ __forceinline__ void interp_pair(const cpair<T>* Y, int K, int mfl, c
   }
 }
 
-// TwoSum-compensated add of v into (sum, comp)
-template <typename T>
-__device__ __forceinline__ void comp_add(T& sum, T& comp, T v) {
-  const T s = sum + v;
-  const T bb = s - sum;
-  comp += (sum - (s - bb)) + (v - bb);
-  sum = s;
-}
-template <typename T>
-__device__ __forceinline__ void comp_add(cpair<T>& s, cpair<T>& c, T w, const cpair<T>& v) {
-  comp_add(s.a.x, c.a.x, w * v.a.x);
-  comp_add(s.a.y, c.a.y, w * v.a.y);
-  comp_add(s.b.x, c.b.x, w * v.b.x);
-  comp_add(s.b.y, c.b.y, w * v.b.y);
-}
+// Adjoint interpolation in scatter form.  Thread t owns samples
+// j = NRES t + rho (rho < NRES; nk <= K/2 = NRES * blockDim).  Stolt
+// positions rise by at least two bins per sample (dp/dj = 4 kappa / p >= 2),
+// so samples of one residue class rho lie >= 2 NRES >= J bins apart and
+// their J-bin neighbourhoods are disjoint: in phase rho every thread adds
+// its sample's J contributions to Y without atomics.  Phases are further
+// split into chunks of K/2 unwrapped bins (chunk = floor(mfl / (K/2))) so
+// that the wrap mod K never folds two neighbourhoods of one phase together.
+// Each bin receives at most ceil(J/2) + 1 contributions per chunk, summed in
+// a fixed order with fused multiply-adds.
+constexpr int NRES = 4;
 
-constexpr int MAXU = 4;              // samples per thread: nk <= K/2 = 4 * (K/8)
-constexpr int BINS_PER_THREAD = 8;   // K / blockDim
-
-// Shared-memory arrays of the adjoint gather, aliasing the FFT buffer.
-template <typename T> struct GatherSmem {
-  cpair<T>* val;            // [nk]  conj(phase) R of both columns
-  T* fr;                    // [nk]  fractional Stolt offset
-  int* m0s;                 // [nk]  first neighbour bin (INT_MIN: evanescent)
-  unsigned short* first;    // [2K]  smallest j reaching a bin of the window
+template <typename T> struct Sample {
+  cpair<T> val;   // conj(phase) R of both columns
+  T frac;         // fractional Stolt offset
+  int mfl;        // unwrapped floor of the Stolt position
+  int chunk;      // INT_MIN: evanescent (no contribution)
 };
+
 template <typename T>
-__device__ __forceinline__ GatherSmem<T> gather_smem(unsigned char* raw, int nk) {
-  GatherSmem<T> g;
-  g.val = reinterpret_cast<cpair<T>*>(raw);
-  g.fr = reinterpret_cast<T*>(g.val + nk);
-  g.m0s = reinterpret_cast<int*>(g.fr + nk);
-  g.first = reinterpret_cast<unsigned short*>(g.m0s + nk);
-  return g;
+__device__ __forceinline__ int chunk_of(int mfl, int K) {
+  const int half = K / 2;
+  return mfl >= 0 ? mfl / half : -((-mfl + half - 1) / half);
 }
 
-// Adjoint interpolation in gather form: after the per-sample arrays are in
-// shared memory, each thread sums the contributions to its bins
-// m = tid + i * blockDim (i < BINS_PER_THREAD) into compensated registers,
-// then (after a barrier) writes Y[prow(m)] -- Y may alias the arrays.
+// Y must be zero; ch_lo/ch_hi bound the chunks of the block's samples.
 template <typename T, int J>
-__device__ __forceinline__ void gather_bins(const AxArgs<T>& A, const GatherSmem<T>& g,
-                                            cpair<T>* Y, int ulo, int uhi) {
+__device__ __forceinline__ void scatter_samples(const AxArgs<T>& A, cpair<T>* Y,
+                                                const Sample<T>* sm, int ch_lo, int ch_hi) {
   using V = cpair<T>;
-  const int K = A.sc.K, nk = A.sc.nk;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  V acc[BINS_PER_THREAD], cmp[BINS_PER_THREAD];
+  const int K = A.sc.K;
+  for (int ch = ch_lo; ch <= ch_hi; ++ch) {
 #pragma unroll
-  for (int i = 0; i < BINS_PER_THREAD; ++i) {
-    acc[i] = {mk<T>(0, 0), mk<T>(0, 0)};
-    cmp[i] = acc[i];
-  }
-  // windows of 2K unwrapped bins (a single window unless near the cut-off)
-  for (int W0 = ulo; W0 <= uhi; W0 += 2 * K) {
-    const int W1 = min(uhi, W0 + 2 * K - 1);
-    // first[u - W0] = smallest j whose neighbourhood m0_j .. m0_j + J - 1 reaches u
-    for (int j = tid; j < nk; j += nt) {
-      const int m0 = g.m0s[j];
-      if (m0 == INT_MIN) continue;
-      const int prev = (j > 0 && g.m0s[j - 1] != INT_MIN) ? g.m0s[j - 1] + J : INT_MIN;
-      const int a = max(max(prev, ulo), W0);
-      const int b = min(m0 + J - 1, W1);
-      for (int u = a; u <= b; ++u) g.first[u - W0] = (unsigned short)j;
-    }
-    __syncthreads();
+    for (int rho = 0; rho < NRES; ++rho) {
+      if (sm[rho].chunk == ch) {
+        T c[J];
+        coefficients<T, J>(A.poly, sm[rho].frac, c);
+        const int m0 = sm[rho].mfl - J / 2 + 1;
+        const V v = sm[rho].val;
 #pragma unroll
-    for (int i = 0; i < BINS_PER_THREAD; ++i) {
-      const int m = tid + i * nt;
-      for (int u = W0 + ((m - W0) & (K - 1)); u <= W1; u += K) {
-        for (int j = g.first[u - W0]; j < nk; ++j) {
-          const int m0 = g.m0s[j];
-          if (m0 > u) break;
-          comp_add(acc[i], cmp[i], coefficient<T, J>(A.poly, g.fr[j], u - m0), g.val[j]);
+        for (int l = 0; l < J; ++l) {
+          const int bi = prow((m0 + l) & (K - 1));
+          V y = Y[bi];
+          y.a.x = fma(c[l], v.a.x, y.a.x);
+          y.a.y = fma(c[l], v.a.y, y.a.y);
+          y.b.x = fma(c[l], v.b.x, y.b.x);
+          y.b.y = fma(c[l], v.b.y, y.b.y);
+          Y[bi] = y;
         }
       }
+      __syncthreads();
     }
-    __syncthreads();
   }
+}
+
+// Zero Y and agree on the chunk range of the block (shared atomics).
+template <typename T>
+__device__ __forceinline__ void prepare_scatter(cpair<T>* Y, int K, const Sample<T>* sm,
+                                                int* ch_lo, int* ch_hi) {
+  const cpair<T> zero = {mk<T>(0, 0), mk<T>(0, 0)};
+  for (int i = threadIdx.x; i < K; i += blockDim.x) Y[prow(i)] = zero;
+  int lo = INT_MAX, hi = INT_MIN;
 #pragma unroll
-  for (int i = 0; i < BINS_PER_THREAD; ++i) Y[prow(tid + i * nt)] = eadd(acc[i], cmp[i]);
+  for (int rho = 0; rho < NRES; ++rho)
+    if (sm[rho].chunk != INT_MIN) {
+      lo = min(lo, sm[rho].chunk);
+      hi = max(hi, sm[rho].chunk);
+    }
+  if (lo != INT_MAX) {
+    atomicMin(ch_lo, lo);
+    atomicMax(ch_hi, hi);
+  }
   __syncthreads();
 }
 
@@ -333,49 +322,42 @@ __global__ void __launch_bounds__(512) k_ax_fwd(const __grid_constant__ AxArgs<T
 }
 
 template <typename T, int J>
-__global__ void __launch_bounds__(512) k_ax_adj(const __grid_constant__ AxArgs<T> A) {
+__global__ void __launch_bounds__(512, 2) k_ax_adj(const __grid_constant__ AxArgs<T> A) {
   using C = cplx<T>;
   using V = cpair<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const StoltConst& sc = A.sc;
-  const int nk = sc.nk;
-  const GatherSmem<T> g = gather_smem<T>(smem_raw, nk);
+  const int K = sc.K, nk = sc.nk;
   V* Y = reinterpret_cast<V*>(smem_raw);
-  __shared__ int u_lo, u_hi;
-  const int tid = threadIdx.x, nt = blockDim.x;
+  __shared__ int ch_lo, ch_hi;
+  const int tid = threadIdx.x;
   int c1, c2, mx, my;
   pair_columns(A, c1, c2, mx, my);
   const bool two = c2 != c1;
-  if (tid == 0) { u_lo = INT_MAX; u_hi = INT_MIN; }
-  __syncthreads();
+  if (tid == 0) { ch_lo = INT_MAX; ch_hi = INT_MIN; }
   const StoltPos<T> sp(sc, mx, my);
   const C* r1 = A.in + size_t(c1) * nk;
   const C* r2 = A.in + size_t(c2) * nk;
-  int lo = INT_MAX, hi = INT_MIN;
-  for (int j = tid; j < nk; j += nt) {
+  Sample<T> sm[NRES];
+#pragma unroll
+  for (int rho = 0; rho < NRES; ++rho) {
+    const int j = NRES * tid + rho;
+    sm[rho].chunk = INT_MIN;
     int mfl;
-    T frac = T(0), turn;
-    V v = {mk<T>(0, 0), mk<T>(0, 0)};
-    int m0 = INT_MIN;
-    if (sp.at(sc, j, mfl, frac, turn)) {
+    T frac, turn;
+    if (j < nk && sp.at(sc, j, mfl, frac, turn)) {
       const C ph = spectral_phase<T>(sc, A.tab.disp, j, turn);
-      v.a = cmulc(r1[j], ph);
-      v.b = two ? cmulc(r2[j], ph) : mk<T>(0, 0);
-      m0 = mfl - J / 2 + 1;
-      lo = min(lo, m0);
-      hi = max(hi, m0);
+      sm[rho].val.a = cmulc(r1[j], ph);
+      sm[rho].val.b = two ? cmulc(r2[j], ph) : mk<T>(0, 0);
+      sm[rho].frac = frac;
+      sm[rho].mfl = mfl;
+      sm[rho].chunk = chunk_of<T>(mfl, K);
     }
-    g.val[j] = v;
-    g.fr[j] = frac;
-    g.m0s[j] = m0;
-  }
-  if (lo != INT_MAX) {
-    atomicMin(&u_lo, lo);
-    atomicMax(&u_hi, hi + J - 1);
   }
   __syncthreads();
-  gather_bins<T, J>(A, g, Y, u_lo, u_hi);
-  fft_smem<-1, T>(Y, 1, 0, tid, sc.K, sc.logK, true);
+  prepare_scatter(Y, K, sm, &ch_lo, &ch_hi);
+  scatter_samples<T, J>(A, Y, sm, ch_lo, ch_hi);
+  fft_smem<-1, T>(Y, 1, 0, tid, K, sc.logK, true);
   store_columns(A, Y, c1, c2, two);
 }
 
@@ -387,39 +369,32 @@ __global__ void __launch_bounds__(512) k_ax_adj(const __grid_constant__ AxArgs<T
 // columns of the pair; then G = N'(conj(phase) R).  F s_d is Hermitian, so
 // only its c1 column is read.  Optionally writes ||R||^2 of the pair.
 template <typename T, int J>
-__global__ void __launch_bounds__(512) k_ax_fused(const __grid_constant__ AxArgs<T> A) {
+__global__ void __launch_bounds__(512, 2) k_ax_fused(const __grid_constant__ AxArgs<T> A) {
   using C = cplx<T>;
   using V = cpair<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const StoltConst& sc = A.sc;
   const int K = sc.K, nk = sc.nk;
   V* Y = reinterpret_cast<V*>(smem_raw);
-  const GatherSmem<T> g = gather_smem<T>(smem_raw, nk);
-  __shared__ int u_lo, u_hi;
+  __shared__ int ch_lo, ch_hi;
   __shared__ double red[16];
   const int tid = threadIdx.x, nt = blockDim.x;
   int c1, c2, mx, my;
   pair_columns(A, c1, c2, mx, my);
   const bool two = c2 != c1;
-  if (tid == 0) { u_lo = INT_MAX; u_hi = INT_MIN; }
+  if (tid == 0) { ch_lo = INT_MAX; ch_hi = INT_MIN; }
   load_and_fft(A, Y, c1, c2, two);
 
   const StoltPos<T> sp(sc, mx, my);
   const C* d1 = A.sdh + size_t(c1) * nk;
-  V vals[MAXU];
-  T frs[MAXU];
-  int m0v[MAXU];
-  int lo = INT_MAX, hi = INT_MIN;
+  Sample<T> sm[NRES];
   double rr = 0.0;
 #pragma unroll
-  for (int u = 0; u < MAXU; ++u) {
-    const int j = tid + u * nt;
-    m0v[u] = INT_MIN;
-    frs[u] = T(0);
-    vals[u] = {mk<T>(0, 0), mk<T>(0, 0)};
+  for (int rho = 0; rho < NRES; ++rho) {
+    const int j = NRES * tid + rho;
+    sm[rho].chunk = INT_MIN;
     if (j >= nk) continue;
     const C dq = d1[j];
-    const C dm = cconj(dq);            // F s_d at -q
     int mfl;
     T frac, turn;
     C s1 = mk<T>(0, 0), s2 = mk<T>(0, 0), ph = mk<T>(0, 0);
@@ -433,54 +408,39 @@ __global__ void __launch_bounds__(512) k_ax_fused(const __grid_constant__ AxArgs
       s2 = two ? cmul(s2, ph) : s1;
     }
     const C R1 = csub(cscale(cadd(s1, cconj(s2)), T(0.5)), dq);
-    const C R2 = csub(cscale(cadd(s2, cconj(s1)), T(0.5)), dm);
+    const C R2 = csub(cscale(cadd(s2, cconj(s1)), T(0.5)), cconj(dq));   // F s_d(-q)
     if (A.partial) {
       rr += double(R1.x) * R1.x + double(R1.y) * R1.y;
       if (two) rr += double(R2.x) * R2.x + double(R2.y) * R2.y;
     }
     if (prop) {
-      vals[u].a = cmulc(R1, ph);
-      vals[u].b = two ? cmulc(R2, ph) : mk<T>(0, 0);
-      frs[u] = frac;
-      m0v[u] = mfl - J / 2 + 1;
-      lo = min(lo, m0v[u]);
-      hi = max(hi, m0v[u]);
+      sm[rho].val.a = cmulc(R1, ph);
+      sm[rho].val.b = two ? cmulc(R2, ph) : mk<T>(0, 0);
+      sm[rho].frac = frac;
+      sm[rho].mfl = mfl;
+      sm[rho].chunk = chunk_of<T>(mfl, K);
     }
-  }
-  __syncthreads();                       // all reads of Y are done: arrays alias it
-#pragma unroll
-  for (int u = 0; u < MAXU; ++u) {
-    const int j = tid + u * nt;
-    if (j >= nk) continue;
-    g.val[j] = vals[u];
-    g.fr[j] = frs[u];
-    g.m0s[j] = m0v[u];
-  }
-  if (lo != INT_MAX) {
-    atomicMin(&u_lo, lo);
-    atomicMax(&u_hi, hi + J - 1);
   }
   if (A.partial) {
     for (int o = 16; o > 0; o >>= 1) rr += __shfl_xor_sync(0xffffffffu, rr, o);
     if ((tid & 31) == 0) red[tid >> 5] = rr;
   }
-  __syncthreads();
+  __syncthreads();                       // all reads of Y are done
   if (A.partial && tid == 0) {
     double t = 0.0;
     for (int w = 0; w < (nt >> 5); ++w) t += red[w];
     A.partial[blockIdx.x] = t;
   }
-  gather_bins<T, J>(A, g, Y, u_lo, u_hi);
+  prepare_scatter(Y, K, sm, &ch_lo, &ch_hi);
+  scatter_samples<T, J>(A, Y, sm, ch_lo, ch_hi);
   fft_smem<-1, T>(Y, 1, 0, tid, K, sc.logK, true);
   store_columns(A, Y, c1, c2, two);
 }
 
 template <typename T> size_t ax_smem_bytes(int K, int nk, bool adj) {
-  const size_t y = size_t(padded_rows(K)) * sizeof(cpair<T>);
-  if (!adj) return y;
-  const size_t arrays = size_t(nk) * (sizeof(cpair<T>) + sizeof(T) + sizeof(int)) +
-                        size_t(2 * K) * sizeof(unsigned short);
-  return y > arrays ? y : arrays;
+  (void)nk;
+  (void)adj;
+  return size_t(padded_rows(K)) * sizeof(cpair<T>);
 }
 template size_t ax_smem_bytes<float>(int, int, bool);
 template size_t ax_smem_bytes<double>(int, int, bool);
