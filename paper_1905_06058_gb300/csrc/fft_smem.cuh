@@ -9,8 +9,8 @@
 // 16- or 32-byte shared-memory access per point).
 //
 // Direction SIGN = -1 computes X_m = sum_p x_p e^{-2 pi i m p / L},
-// SIGN = +1 the same with e^{+...}; no normalisation.  Twiddles are computed
-// per butterfly: one sincospi of the exact rational angle, then powers.
+// SIGN = +1 the same with e^{+...}; no normalisation.  Twiddles come from a
+// per-block shared-memory table (build_twiddles).
 #pragma once
 
 #include "common.cuh"
@@ -71,8 +71,24 @@ __device__ __forceinline__ void dft4(E& a0, E& a1, E& a2, E& a3) {
   a1 = eadd(t1, t3); a3 = esub(t1, t3);
 }
 
-template <int SIGN, typename E>
+template <int SIGN, bool HALF_ZERO = false, typename E>
 __device__ __forceinline__ void dft8(E* a) {
+  if (HALF_ZERO) {
+    // a[2..5] == 0: even part (a0, 0, 0, a6), odd part (a1, 0, 0, a7)
+    const E e0 = eadd(a[0], a[6]), e2 = esub(a[0], a[6]);
+    const E i6 = emul_i<SIGN>(a[6]);
+    const E e1 = esub(a[0], i6), e3 = eadd(a[0], i6);
+    const E o0 = eadd(a[1], a[7]), o2 = esub(a[1], a[7]);
+    const E i7 = emul_i<SIGN>(a[7]);
+    const E o1 = ew8_1<SIGN>(esub(a[1], i7));
+    const E o2w = emul_i<SIGN>(o2);
+    const E o3 = ew8_3<SIGN>(eadd(a[1], i7));
+    a[0] = eadd(e0, o0); a[4] = esub(e0, o0);
+    a[1] = eadd(e1, o1); a[5] = esub(e1, o1);
+    a[2] = eadd(e2, o2w); a[6] = esub(e2, o2w);
+    a[3] = eadd(e3, o3); a[7] = esub(e3, o3);
+    return;
+  }
   dft4<SIGN>(a[0], a[2], a[4], a[6]);
   dft4<SIGN>(a[1], a[3], a[5], a[7]);
   // odd half times W8^k, W8 = e^{SIGN 2 pi i / 8}
@@ -97,31 +113,60 @@ __host__ __device__ __forceinline__ int padded_rows(int L) { return L + (L >> 3)
 __device__ __forceinline__ void sincospi_(float x, float* s, float* c) { sincospif(x, s, c); }
 __device__ __forceinline__ void sincospi_(double x, double* s, double* c) { sincospi(x, s, c); }
 
-// w[r] = e^{SIGN 2 pi i r k / N} for r = 1..R-1: one sincospi, then powers.
-template <int SIGN, int R, typename T>
-__device__ __forceinline__ void twiddles(int k, int N, cplx<T>* w) {
-  T s, c;
-  sincospi_(T(2 * k) / T(N), &s, &c);
-  w[1] = mk<T>(c, SIGN * s);
-  if (R >= 4) {
-    w[2] = cmul(w[1], w[1]);
-    w[3] = cmul(w[2], w[1]);
+// Twiddle table of an L-point transform, in shared memory: for every pass
+// with span Ns > 1 and radix R, entries k (R-1) + (r-1) of that pass's
+// segment hold e^{-2 pi i r k / (Ns R)}, k < Ns, 1 <= r < R.  Threads with
+// consecutive k read consecutive (R-1)-entry rows: no bank conflicts.
+__host__ __device__ __forceinline__ int twiddle_entries(int L, int logL) {
+  if (L < 8) return 0;
+  int n = 0, Ns = 1;
+  const int n8 = logL / 3;
+  for (int p = 0; p < n8; ++p) {
+    if (Ns > 1) n += Ns * 7;
+    Ns *= 8;
   }
-  if (R == 8) {
-    w[4] = cmul(w[2], w[2]);
-    w[5] = cmul(w[4], w[1]);
-    w[6] = cmul(w[3], w[3]);
-    w[7] = cmul(w[4], w[3]);
+  const int rem = logL - 3 * n8;
+  if (rem == 2 && Ns > 1) n += Ns * 3;
+  if (rem == 1 && Ns > 1) n += Ns;
+  return n;
+}
+
+// All threads of the block fill the table (ends with a barrier).
+template <typename T>
+__device__ __forceinline__ void build_twiddles(cplx<T>* tab, int L, int logL) {
+  if (L >= 8) {
+    const int n8 = logL / 3, rem = logL - 3 * n8;
+    const int npass = n8 + (rem ? 1 : 0);
+    int off = 0, Ns = 1;
+    for (int p = 0; p < npass; ++p) {
+      const int R = p < n8 ? 8 : (rem == 2 ? 4 : 2);
+      if (Ns > 1) {
+        for (int k = threadIdx.x; k < Ns; k += blockDim.x) {
+          T s, c;
+          sincospi_(T(2 * k) / T(Ns * R), &s, &c);
+          const cplx<T> w1 = mk<T>(c, -s);
+          cplx<T> w = w1;
+          for (int r = 1; r < R; ++r) {
+            tab[off + k * (R - 1) + (r - 1)] = w;
+            w = cmul(w, w1);
+          }
+        }
+        off += Ns * (R - 1);
+      }
+      Ns *= R;
+    }
   }
+  __syncthreads();
 }
 
 // One Stockham pass of radix R on column `col` (logical row r at
 // buf[prow(r)*stride+col]); this thread does 8/R butterflies j = b + u * (L/8).
-// Reads all its inputs, block barrier, writes.  Every thread of the block
-// must reach it.
-template <int SIGN, int R, typename T, typename E>
+// tw is this pass's twiddle segment.  HALF_ZERO: input rows in [L/4, 3L/4)
+// are known zero and not read (first pass of a twice zero-padded transform).
+// Reads all its inputs, block barrier, writes.  Every thread must reach it.
+template <int SIGN, int R, bool HALF_ZERO, typename T, typename E>
 __device__ __forceinline__ void stockham_pass(E* buf, int stride, int col, int b, int L,
-                                              int Ns, bool active) {
+                                              int Ns, const cplx<T>* tw, bool active) {
   constexpr int NB = 8 / R;          // butterflies per thread
   const int LR = L / R;
   const int L8 = L >> 3;
@@ -131,7 +176,13 @@ __device__ __forceinline__ void stockham_pass(E* buf, int stride, int col, int b
     for (int u = 0; u < NB; ++u) {
       const int j = b + u * L8;
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[u * R + r] = buf[prow(j + r * LR) * stride + col];
+      for (int r = 0; r < R; ++r) {
+        if (HALF_ZERO && R == 8 && r >= 2 && r <= 5) {
+          v[u * R + r] = E{};
+        } else {
+          v[u * R + r] = buf[prow(j + r * LR) * stride + col];
+        }
+      }
     }
   }
   __syncthreads();
@@ -142,12 +193,14 @@ __device__ __forceinline__ void stockham_pass(E* buf, int stride, int col, int b
       const int k = j & (Ns - 1);
       E* a = v + u * R;
       if (Ns > 1) {
-        cplx<T> w[8];
-        twiddles<SIGN, R, T>(k, Ns * R, w);
 #pragma unroll
-        for (int r = 1; r < R; ++r) a[r] = emul(a[r], w[r]);
+        for (int r = 1; r < R; ++r) {
+          cplx<T> w = tw[k * (R - 1) + (r - 1)];
+          if (SIGN > 0) w.y = -w.y;
+          a[r] = emul(a[r], w);
+        }
       }
-      if (R == 8) dft8<SIGN>(a);
+      if (R == 8) dft8<SIGN, HALF_ZERO>(a);
       else if (R == 4) dft4<SIGN>(a[0], a[1], a[2], a[3]);
       else dft2<SIGN>(a[0], a[1]);
       const int base = (j - k) * R + k;
@@ -158,23 +211,28 @@ __device__ __forceinline__ void stockham_pass(E* buf, int stride, int col, int b
   __syncthreads();
 }
 
-// Length-L transform (L = 2^logL, 1 <= L <= 8192) of column `col`.  For
-// L >= 8 the active threads own butterfly b < L/8; for L < 8 the thread with
-// b == 0 transforms the column directly.  Every thread of the block must call
-// it (it contains barriers); it ends with a barrier.
-template <int SIGN, typename T, typename E>
+// Length-L transform (L = 2^logL, 1 <= L <= 8192) of column `col`, using the
+// twiddle table built by build_twiddles.  For L >= 8 the active threads own
+// butterfly b < L/8; for L < 8 the thread with b == 0 transforms the column
+// directly.  HALF_ZERO: rows [L/4, 3L/4) of the input are zero (and need not
+// be stored).  Every thread of the block must call it; it ends with a barrier.
+template <int SIGN, bool HALF_ZERO, typename T, typename E>
 __device__ __forceinline__ void fft_smem(E* buf, int stride, int col, int b, int L, int logL,
-                                         bool active) {
+                                         const cplx<T>* tw, bool active) {
   if (L >= 8) {
     int Ns = 1;
     const int n8 = logL / 3;
     for (int p = 0; p < n8; ++p) {
-      stockham_pass<SIGN, 8, T>(buf, stride, col, b, L, Ns, active);
+      if (p == 0 && HALF_ZERO)
+        stockham_pass<SIGN, 8, true, T>(buf, stride, col, b, L, Ns, tw, active);
+      else
+        stockham_pass<SIGN, 8, false, T>(buf, stride, col, b, L, Ns, tw, active);
+      if (Ns > 1) tw += Ns * 7;
       Ns *= 8;
     }
     const int rem = logL - 3 * n8;
-    if (rem == 2) stockham_pass<SIGN, 4, T>(buf, stride, col, b, L, Ns, active);
-    else if (rem == 1) stockham_pass<SIGN, 2, T>(buf, stride, col, b, L, Ns, active);
+    if (rem == 2) stockham_pass<SIGN, 4, false, T>(buf, stride, col, b, L, Ns, tw, active);
+    else if (rem == 1) stockham_pass<SIGN, 2, false, T>(buf, stride, col, b, L, Ns, tw, active);
   } else {
     __syncthreads();
     if (active && b == 0 && L > 1) {

@@ -28,6 +28,7 @@
 namespace isam {
 
 __device__ __forceinline__ int signed_freq(int i, int n) { return i <= (n - 1) / 2 ? i : i - n; }
+static inline int ilog2_dev(int v) { int r = 0; while ((1 << r) < v) ++r; return r; }
 
 template <typename T> struct StoltPos;
 
@@ -151,18 +152,24 @@ __device__ __forceinline__ void pair_columns(const AxArgs<T>& A, int& c1, int& c
   my = signed_freq(c1 / A.sc.nx, A.sc.ny);
 }
 
-// Y (padded rows) = scaled, zero-padded columns c1 (a) and c2 (b), then the
-// K-point e^{+} DFT.  Ends with a barrier.
+// Shared memory of the axial kernels: the FFT buffer Y (padded rows of
+// column pairs) followed by the K-point twiddle table.
 template <typename T>
-__device__ __forceinline__ void load_and_fft(const AxArgs<T>& A, cpair<T>* Y, int c1, int c2,
-                                             bool two) {
+__device__ __forceinline__ cplx<T>* twiddle_table(unsigned char* raw, int K) {
+  return reinterpret_cast<cplx<T>*>(raw + size_t(padded_rows(K)) * sizeof(cpair<T>));
+}
+
+// Y (padded rows) = scaled columns c1 (a) and c2 (b), zero-padded to K, then
+// the K-point e^{+} DFT.  The padding rows [nz/2, K - nz/2) are never stored:
+// the first FFT pass knows them to be zero.  Ends with a barrier.
+template <typename T>
+__device__ __forceinline__ void load_and_fft(const AxArgs<T>& A, cpair<T>* Y, const cplx<T>* tw,
+                                             int c1, int c2, bool two) {
   using C = cplx<T>;
   using V = cpair<T>;
   const StoltConst& sc = A.sc;
   const int K = sc.K, nz = sc.nz;
   const int tid = threadIdx.x, nt = blockDim.x;
-  const V zero = {mk<T>(0, 0), mk<T>(0, 0)};
-  for (int i = nz / 2 + tid; i < K - nz / 2; i += nt) Y[prow(i)] = zero;
   const C* x1 = A.in + size_t(c1) * nz;
   const C* x2 = A.in + size_t(c2) * nz;
   for (int n = tid; n < nz; n += nt) {
@@ -175,7 +182,7 @@ __device__ __forceinline__ void load_and_fft(const AxArgs<T>& A, cpair<T>* Y, in
     Y[prow(p)] = v;
   }
   __syncthreads();
-  fft_smem<+1, T>(Y, 1, 0, tid, K, sc.logK, true);
+  fft_smem<+1, true, T>(Y, 1, 0, tid, K, sc.logK, tw, true);
 }
 
 // forward interpolation of both columns at sample j (before the phase)
@@ -214,19 +221,50 @@ template <typename T> struct Sample {
   int chunk;      // INT_MIN: evanescent (no contribution)
 };
 
-template <typename T>
-__device__ __forceinline__ int chunk_of(int mfl, int K) {
-  const int half = K / 2;
-  return mfl >= 0 ? mfl / half : -((-mfl + half - 1) / half);
+// Zero Y, find the block's range of Stolt positions (shared atomics on
+// *lo, *hi, initialised by the caller before an earlier barrier) and assign
+// every sample to a chunk of width K - J of unwrapped positions: within a
+// chunk the J-bin neighbourhoods span fewer than K bins, so they never meet
+// again after the wrap mod K.  Returns the number of chunks.
+template <typename T, int J>
+__device__ __forceinline__ int prepare_scatter(cpair<T>* Y, int K, Sample<T>* sm, int* lo,
+                                               int* hi) {
+  const cpair<T> zero = {mk<T>(0, 0), mk<T>(0, 0)};
+  for (int i = threadIdx.x; i < K; i += blockDim.x) Y[prow(i)] = zero;
+  int l = INT_MAX, h = INT_MIN;
+#pragma unroll
+  for (int rho = 0; rho < NRES; ++rho)
+    if (sm[rho].chunk != INT_MIN) {
+      l = min(l, sm[rho].mfl);
+      h = max(h, sm[rho].mfl);
+    }
+  if (l != INT_MAX) {
+    atomicMin(lo, l);
+    atomicMax(hi, h);
+  }
+  __syncthreads();
+  const int base = *lo, width = K - J;
+  if (base == INT_MAX) return 0;
+#pragma unroll
+  for (int rho = 0; rho < NRES; ++rho)
+    if (sm[rho].chunk != INT_MIN) {
+      int c = 0, d = sm[rho].mfl - base;
+      while (d >= width) { d -= width; ++c; }
+      sm[rho].chunk = c;
+    }
+  int n = 1;
+  for (int d = *hi - base; d >= width; d -= width) ++n;
+  return n;
 }
 
-// Y must be zero; ch_lo/ch_hi bound the chunks of the block's samples.
+// Y must be zero; every thread adds its samples' J contributions, residue
+// class by residue class and chunk by chunk (see the comment above NRES).
 template <typename T, int J>
 __device__ __forceinline__ void scatter_samples(const AxArgs<T>& A, cpair<T>* Y,
-                                                const Sample<T>* sm, int ch_lo, int ch_hi) {
+                                                const Sample<T>* sm, int nchunks) {
   using V = cpair<T>;
   const int K = A.sc.K;
-  for (int ch = ch_lo; ch <= ch_hi; ++ch) {
+  for (int ch = 0; ch < nchunks; ++ch) {
 #pragma unroll
     for (int rho = 0; rho < NRES; ++rho) {
       if (sm[rho].chunk == ch) {
@@ -248,26 +286,6 @@ __device__ __forceinline__ void scatter_samples(const AxArgs<T>& A, cpair<T>* Y,
       __syncthreads();
     }
   }
-}
-
-// Zero Y and agree on the chunk range of the block (shared atomics).
-template <typename T>
-__device__ __forceinline__ void prepare_scatter(cpair<T>* Y, int K, const Sample<T>* sm,
-                                                int* ch_lo, int* ch_hi) {
-  const cpair<T> zero = {mk<T>(0, 0), mk<T>(0, 0)};
-  for (int i = threadIdx.x; i < K; i += blockDim.x) Y[prow(i)] = zero;
-  int lo = INT_MAX, hi = INT_MIN;
-#pragma unroll
-  for (int rho = 0; rho < NRES; ++rho)
-    if (sm[rho].chunk != INT_MIN) {
-      lo = min(lo, sm[rho].chunk);
-      hi = max(hi, sm[rho].chunk);
-    }
-  if (lo != INT_MAX) {
-    atomicMin(ch_lo, lo);
-    atomicMax(ch_hi, hi);
-  }
-  __syncthreads();
 }
 
 // Y (after the e^{-} DFT): truncate to the nz samples, scale, store columns.
@@ -296,10 +314,12 @@ __global__ void __launch_bounds__(512) k_ax_fwd(const __grid_constant__ AxArgs<T
   const StoltConst& sc = A.sc;
   const int K = sc.K, nk = sc.nk;
   V* Y = reinterpret_cast<V*>(smem_raw);
+  cplx<T>* tw = twiddle_table<T>(smem_raw, K);
   int c1, c2, mx, my;
   pair_columns(A, c1, c2, mx, my);
   const bool two = c2 != c1;
-  load_and_fft(A, Y, c1, c2, two);
+  build_twiddles<T>(tw, K, sc.logK);
+  load_and_fft(A, Y, tw, c1, c2, two);
 
   const StoltPos<T> sp(sc, mx, my);
   C* o1 = A.out + size_t(c1) * nk;
@@ -329,12 +349,14 @@ __global__ void __launch_bounds__(512, 2) k_ax_adj(const __grid_constant__ AxArg
   const StoltConst& sc = A.sc;
   const int K = sc.K, nk = sc.nk;
   V* Y = reinterpret_cast<V*>(smem_raw);
+  cplx<T>* tw = twiddle_table<T>(smem_raw, K);
   __shared__ int ch_lo, ch_hi;
   const int tid = threadIdx.x;
   int c1, c2, mx, my;
   pair_columns(A, c1, c2, mx, my);
   const bool two = c2 != c1;
   if (tid == 0) { ch_lo = INT_MAX; ch_hi = INT_MIN; }
+  build_twiddles<T>(tw, K, sc.logK);
   const StoltPos<T> sp(sc, mx, my);
   const C* r1 = A.in + size_t(c1) * nk;
   const C* r2 = A.in + size_t(c2) * nk;
@@ -351,13 +373,12 @@ __global__ void __launch_bounds__(512, 2) k_ax_adj(const __grid_constant__ AxArg
       sm[rho].val.b = two ? cmulc(r2[j], ph) : mk<T>(0, 0);
       sm[rho].frac = frac;
       sm[rho].mfl = mfl;
-      sm[rho].chunk = chunk_of<T>(mfl, K);
+      sm[rho].chunk = 0;
     }
   }
-  __syncthreads();
-  prepare_scatter(Y, K, sm, &ch_lo, &ch_hi);
-  scatter_samples<T, J>(A, Y, sm, ch_lo, ch_hi);
-  fft_smem<-1, T>(Y, 1, 0, tid, K, sc.logK, true);
+  const int nch = prepare_scatter<T, J>(Y, K, sm, &ch_lo, &ch_hi);
+  scatter_samples<T, J>(A, Y, sm, nch);
+  fft_smem<-1, false, T>(Y, 1, 0, tid, K, sc.logK, tw, true);
   store_columns(A, Y, c1, c2, two);
 }
 
@@ -376,6 +397,7 @@ __global__ void __launch_bounds__(512, 2) k_ax_fused(const __grid_constant__ AxA
   const StoltConst& sc = A.sc;
   const int K = sc.K, nk = sc.nk;
   V* Y = reinterpret_cast<V*>(smem_raw);
+  cplx<T>* tw = twiddle_table<T>(smem_raw, K);
   __shared__ int ch_lo, ch_hi;
   __shared__ double red[16];
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -383,7 +405,8 @@ __global__ void __launch_bounds__(512, 2) k_ax_fused(const __grid_constant__ AxA
   pair_columns(A, c1, c2, mx, my);
   const bool two = c2 != c1;
   if (tid == 0) { ch_lo = INT_MAX; ch_hi = INT_MIN; }
-  load_and_fft(A, Y, c1, c2, two);
+  build_twiddles<T>(tw, K, sc.logK);
+  load_and_fft(A, Y, tw, c1, c2, two);
 
   const StoltPos<T> sp(sc, mx, my);
   const C* d1 = A.sdh + size_t(c1) * nk;
@@ -418,7 +441,7 @@ __global__ void __launch_bounds__(512, 2) k_ax_fused(const __grid_constant__ AxA
       sm[rho].val.b = two ? cmulc(R2, ph) : mk<T>(0, 0);
       sm[rho].frac = frac;
       sm[rho].mfl = mfl;
-      sm[rho].chunk = chunk_of<T>(mfl, K);
+      sm[rho].chunk = 0;
     }
   }
   if (A.partial) {
@@ -431,16 +454,17 @@ __global__ void __launch_bounds__(512, 2) k_ax_fused(const __grid_constant__ AxA
     for (int w = 0; w < (nt >> 5); ++w) t += red[w];
     A.partial[blockIdx.x] = t;
   }
-  prepare_scatter(Y, K, sm, &ch_lo, &ch_hi);
-  scatter_samples<T, J>(A, Y, sm, ch_lo, ch_hi);
-  fft_smem<-1, T>(Y, 1, 0, tid, K, sc.logK, true);
+  const int nch = prepare_scatter<T, J>(Y, K, sm, &ch_lo, &ch_hi);
+  scatter_samples<T, J>(A, Y, sm, nch);
+  fft_smem<-1, false, T>(Y, 1, 0, tid, K, sc.logK, tw, true);
   store_columns(A, Y, c1, c2, two);
 }
 
 template <typename T> size_t ax_smem_bytes(int K, int nk, bool adj) {
   (void)nk;
   (void)adj;
-  return size_t(padded_rows(K)) * sizeof(cpair<T>);
+  return size_t(padded_rows(K)) * sizeof(cpair<T>) +
+         size_t(twiddle_entries(K, ilog2_dev(K))) * sizeof(cplx<T>);
 }
 template size_t ax_smem_bytes<float>(int, int, bool);
 template size_t ax_smem_bytes<double>(int, int, bool);

@@ -58,6 +58,8 @@ __global__ void __launch_bounds__(512) k_lat(const __grid_constant__ LatArgs<T> 
   V* buf = reinterpret_cast<V*>(smem_raw);
   const int tid = threadIdx.x, nt = blockDim.x;
   const int TP = a.TZ, L = a.L, logTP = a.logTZ;
+  cplx<T>* tw = reinterpret_cast<cplx<T>*>(buf + size_t(padded_rows(L)) * TP);
+  build_twiddles<T>(tw, L, a.logL);
   const int col = tid & (TP - 1), b = tid >> logTP;
   const size_t M = size_t(a.M);
   const size_t m_first = size_t(blockIdx.x) * (2 * TP);
@@ -81,9 +83,9 @@ __global__ void __launch_bounds__(512) k_lat(const __grid_constant__ LatArgs<T> 
   __syncthreads();
 
   if (MODE == LAT_C2C_FWD || MODE == LAT_R2C_FWD)
-    fft_smem<-1, T>(buf, TP, col, b, L, a.logL, true);
+    fft_smem<-1, false, T>(buf, TP, col, b, L, a.logL, tw, true);
   else
-    fft_smem<+1, T>(buf, TP, col, b, L, a.logL, true);
+    fft_smem<+1, false, T>(buf, TP, col, b, L, a.logL, tw, true);
 
   const T nrm = a.norm;
   if (MODE == LAT_C2C_FWD || MODE == LAT_C2C_INV || MODE == LAT_R2C_FWD) {
@@ -141,7 +143,7 @@ __global__ void __launch_bounds__(512) k_lat(const __grid_constant__ LatArgs<T> 
   }
   if (bad) atomicOr(a.flag, 1);
   __syncthreads();
-  fft_smem<-1, T>(buf, TP, col, b, L, a.logL, true);
+  fft_smem<-1, false, T>(buf, TP, col, b, L, a.logL, tw, true);
   C* out = static_cast<C*>(a.out);
   for (int e = tid; e < n_el; e += nt) {
     const int row = e >> logTP, c = e & (TP - 1);
@@ -170,8 +172,11 @@ __global__ void __launch_bounds__(512) k_lat(const __grid_constant__ LatArgs<T> 
   }
 }
 
+static int ilog2_host(int v) { int r = 0; while ((1 << r) < v) ++r; return r; }
+
 template <typename T> size_t lat_smem_bytes(int L, int TP) {
-  return size_t(padded_rows(L)) * TP * sizeof(cpair<T>);
+  return size_t(padded_rows(L)) * TP * sizeof(cpair<T>) +
+         size_t(twiddle_entries(L, ilog2_host(L))) * sizeof(cplx<T>);
 }
 
 template <typename T, int MODE>
