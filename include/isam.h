@@ -143,6 +143,22 @@ isam_status isam_lipschitz(isam_plan* plan, int32_t iters, double rtol, const vo
 /* max |eta_i| of a device image (used for lambda = c ||A^H s||_inf).  Synchronous. */
 isam_status isam_max_abs(isam_plan* plan, const void* eta, double* out);
 
+/* max |x_i| over n complex device elements (FP32: float2, FP64: double2),
+ * written to the device double *out; asynchronous on `stream`.  It allocates
+ * nothing, for callers that cannot: a thread recording a stream capture owned
+ * by another framework, an acquisition loop whose memory was fixed at
+ * start-up, or code whose device memory is held by a pooling allocator.  The
+ * paper has no counterpart; it is the reduction behind lambda = c ||A^H s||_inf.
+ * Scratch is a static device array of ISAM_NOALLOC_MAX_PARTIALS doubles
+ * (512 KiB, held by every GPU that loads the library until exit); n above
+ * ISAM_NOALLOC_MAX_PARTIALS * 2048 returns ISAM_ERR_UNSUPPORTED.  The first
+ * call on a device looks the array's address up (cudaGetSymbolAddress) and
+ * must come before any stream capture.  Calls share the array: calls that
+ * overlap on the GPU race and must be serialised by the caller. */
+#define ISAM_NOALLOC_MAX_PARTIALS 65536
+isam_status isam_max_abs_noalloc(const void* x, int64_t n, int32_t precision, double* out,
+                                 void* stream);
+
 /* Kernel launches issued by the last isam_forward / isam_adjoint / isam_solve. */
 int64_t isam_last_launch_count(const isam_plan* plan);
 
