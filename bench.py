@@ -362,9 +362,36 @@ def run_extras(torch, plan, s_d, wl, args, L):
     torch.cuda.synchronize()
     ex["fp64_iters_per_s"] = it64 / (a.elapsed_time(b) / 1000.0)
     p64.close()
+    ex["cufft_comparison_us"] = cufft_comparison(torch, plan)
     if args.volume:
         ex["volume"] = run_volume(torch)
     return ex
+
+
+def cufft_comparison(torch, plan):
+    """cuFFT (through torch.fft) on the transforms one FISTA iteration needs, for
+    comparison with the hand-written kernels: two lateral FFTs (forward and
+    inverse, length nx over nz columns) and two zero-padded axial FFTs (length
+    K = 2 nz over nx columns).  Device time per call, microseconds."""
+    ny, nx, nz = plan.image_shape
+    x = torch.randn(nx, nz, dtype=torch.complex64, device="cuda")
+    y = torch.randn(nx, nz, dtype=torch.complex64, device="cuda")
+    out = {}
+    for name, fn in (("lateral_fft_nx", lambda: torch.fft.fft(x, dim=0)),
+                     ("axial_fft_2nz_zero_padded", lambda: torch.fft.fft(y, n=2 * nz, dim=1))):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 50
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        out[name] = a.elapsed_time(b) / reps * 1000.0
+    out["per_iteration_4_ffts"] = 2 * out["lateral_fft_nx"] + 2 * out["axial_fft_2nz_zero_padded"]
+    return out
 
 
 def run_volume(torch):
