@@ -172,6 +172,21 @@ def algorithmic_bytes(cls: str, n_img: int, n_spec: int, real_bytes=4) -> int:
 NCU_TRAFFIC = {}
 
 
+def reduce_over_ranks(torch, elapsed, units, world, device):
+    """Whole-job timing: the slowest rank's elapsed time and the units (FISTA
+    iterations) of all ranks.  Ranks solve independent problems, so this scalar
+    reduction is the only collective."""
+    if world <= 1:
+        return float(elapsed), float(units)
+    import torch.distributed as dist
+    t = torch.tensor([float(elapsed)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.barrier()
+    return float(t[0]), float(u[0])
+
+
 def make_problem(torch, plan, wl, seed):
     from paper_1905_06058_gb300 import inputs as I
     eta = torch.from_numpy(wl.eta.astype(np.complex64)).cuda()
@@ -242,15 +257,7 @@ def run_ours(args):
         plan.solve(s_d, out=out, **opts)
     prof = plan.profile_read()
     plan.profile(False)
-    if world > 1:
-        t = torch.tensor([total_ms, iters_done], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        torch.distributed.all_reduce(tmax[:1], op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(t[1:], op=torch.distributed.ReduceOp.SUM)
-        total_ms, all_iters = float(tmax[0]), float(t[1])
-        torch.distributed.barrier()
-    else:
-        all_iters = iters_done
+    total_ms, all_iters = reduce_over_ranks(torch, total_ms, iters_done, world, "cuda")
     value = all_iters / (total_ms / 1000.0)
 
     # dominant kernel and its live roofline
@@ -285,12 +292,7 @@ def run_ours(args):
         e2e_iters += info["iterations"]
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s, e2e_iters], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t[:1], op=torch.distributed.ReduceOp.MAX)
-        tt = t[1:].clone()
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.SUM)
-        e2e_s, e2e_iters = float(t[0]), float(tt[0])
+    e2e_s, e2e_iters = reduce_over_ranks(torch, e2e_s, e2e_iters, world, "cuda")
     e2e = {"value": e2e_iters / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": int(s_h.numel() * 4), "d2h_bytes_per_step": int(o_h.numel() * 8)}
 

@@ -42,12 +42,13 @@ template <> struct StoltPos<float> {
   }
   __device__ __forceinline__ bool at(const StoltConst& c, int j, int& mfl, float& frac,
                                      float& turn) const {
-    const ff kap = ff_add({c.kap_hi, c.kap_lo}, {float(j), 0.0f});
+    ff kap = ff_two_sum(c.kap_hi, float(j));            // j is an exact integer
+    kap = ff_quick(kap.hi, kap.lo + c.kap_lo);
     ff k2 = ff_mul(kap, kap);
     k2.hi *= 4.0f; k2.lo *= 4.0f;                       // exact
     const ff x = ff_sub(k2, a);
     if (!(x.hi > 0.0f)) return false;
-    const ff p = ff_sqrt(x);
+    const ff p = ff_sqrt_fast(x);
     ff t = ff_two_sum(p.hi, -c.B);
     t.lo += p.lo;
     float fl = floorf(t.hi);
@@ -172,14 +173,20 @@ __device__ __forceinline__ void load_and_fft(const AxArgs<T>& A, cpair<T>* Y, co
   const int tid = threadIdx.x, nt = blockDim.x;
   const C* x1 = A.in + size_t(c1) * nz;
   const C* x2 = A.in + size_t(c2) * nz;
-  for (int n = tid; n < nz; n += nt) {
+  // nz = 4 * blockDim: four samples per thread, loads issued before use
+  V v[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int n = tid + i * nt;
+    v[i].a = x1[n];
+    v[i].b = two ? x2[n] : mk<T>(0, 0);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int n = tid + i * nt;
     int p = n - nz / 2;
     if (p < 0) p += K;
-    const T s = __ldg(A.tab.scale + n);
-    V v;
-    v.a = cscale(x1[n], s);
-    v.b = two ? cscale(x2[n], s) : mk<T>(0, 0);
-    Y[prow(p)] = v;
+    Y[prow(p)] = escale(v[i], __ldg(A.tab.scale + n));
   }
   __syncthreads();
   fft_smem<+1, true, T>(Y, 1, 0, tid, K, sc.logK, tw, true);
@@ -405,11 +412,18 @@ __global__ void __launch_bounds__(512, 2) k_ax_fused(const __grid_constant__ AxA
   pair_columns(A, c1, c2, mx, my);
   const bool two = c2 != c1;
   if (tid == 0) { ch_lo = INT_MAX; ch_hi = INT_MIN; }
+  // F s_d at this pair's samples, fetched before the transforms need them
+  const C* d1 = A.sdh + size_t(c1) * nk;
+  C dqv[NRES];
+#pragma unroll
+  for (int rho = 0; rho < NRES; ++rho) {
+    const int j = NRES * tid + rho;
+    dqv[rho] = j < nk ? d1[j] : mk<T>(0, 0);
+  }
   build_twiddles<T>(tw, K, sc.logK);
   load_and_fft(A, Y, tw, c1, c2, two);
 
   const StoltPos<T> sp(sc, mx, my);
-  const C* d1 = A.sdh + size_t(c1) * nk;
   Sample<T> sm[NRES];
   double rr = 0.0;
 #pragma unroll
@@ -417,7 +431,7 @@ __global__ void __launch_bounds__(512, 2) k_ax_fused(const __grid_constant__ AxA
     const int j = NRES * tid + rho;
     sm[rho].chunk = INT_MIN;
     if (j >= nk) continue;
-    const C dq = d1[j];
+    const C dq = dqv[rho];
     int mfl;
     T frac, turn;
     C s1 = mk<T>(0, 0), s2 = mk<T>(0, 0), ph = mk<T>(0, 0);

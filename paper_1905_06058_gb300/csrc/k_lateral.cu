@@ -50,7 +50,7 @@ template <> struct rpair_t<float> { using type = float2; };
 template <> struct rpair_t<double> { using type = double2; };
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(512) k_lat(const __grid_constant__ LatArgs<T> a) {
+__global__ void __launch_bounds__(512, 2) k_lat(const __grid_constant__ LatArgs<T> a) {
   using C = cplx<T>;
   using V = cpair<T>;
   using RP = typename rpair_t<T>::type;   // two adjacent reals
@@ -66,19 +66,32 @@ __global__ void __launch_bounds__(512) k_lat(const __grid_constant__ LatArgs<T> 
   const size_t base = size_t(blockIdx.y) * size_t(L) * M + m_first;
   const int n_el = L * TP;
 
-  // load the tile (element e: row e / TP, pair-column e % TP)
-  for (int e = tid; e < n_el; e += nt) {
-    const int row = e >> logTP, c = e & (TP - 1);
-    const size_t gi = base + size_t(row) * M + 2 * c;
-    V v;
-    if (MODE == LAT_R2C_FWD) {
-      const RP r = *reinterpret_cast<const RP*>(static_cast<const T*>(a.in) + gi);
-      v.a = mk<T>(r.x, T(0));
-      v.b = mk<T>(r.y, T(0));
-    } else {
-      v = *reinterpret_cast<const V*>(static_cast<const C*>(a.in) + gi);
+  // Every thread owns ept = n_el / blockDim elements (8 for L >= 8):
+  // element i of a thread is e = tid + i * nt (row e / TP, pair-column e % TP).
+  const int ept = n_el / nt;
+  auto gidx = [&](int e) { return base + size_t(e >> logTP) * M + 2 * (e & (TP - 1)); };
+  auto sidx = [&](int e) { return prow(e >> logTP) * TP + (e & (TP - 1)); };
+
+  // load the tile: all global loads first, then the shared-memory stores
+  {
+    V v[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      if (i >= ept) break;
+      const size_t gi = gidx(tid + i * nt);
+      if (MODE == LAT_R2C_FWD) {
+        const RP r = *reinterpret_cast<const RP*>(static_cast<const T*>(a.in) + gi);
+        v[i].a = mk<T>(r.x, T(0));
+        v[i].b = mk<T>(r.y, T(0));
+      } else {
+        v[i] = *reinterpret_cast<const V*>(static_cast<const C*>(a.in) + gi);
+      }
     }
-    buf[prow(row) * TP + c] = v;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      if (i >= ept) break;
+      buf[sidx(tid + i * nt)] = v[i];
+    }
   }
   __syncthreads();
 
@@ -90,65 +103,80 @@ __global__ void __launch_bounds__(512) k_lat(const __grid_constant__ LatArgs<T> 
   const T nrm = a.norm;
   if (MODE == LAT_C2C_FWD || MODE == LAT_C2C_INV || MODE == LAT_R2C_FWD) {
     C* out = static_cast<C*>(a.out);
-    for (int e = tid; e < n_el; e += nt) {
-      const int row = e >> logTP, c = e & (TP - 1);
-      const size_t gi = base + size_t(row) * M + 2 * c;
-      *reinterpret_cast<V*>(out + gi) = escale(buf[prow(row) * TP + c], nrm);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      if (i >= ept) break;
+      const int e = tid + i * nt;
+      *reinterpret_cast<V*>(out + gidx(e)) = escale(buf[sidx(e)], nrm);
     }
     return;
   }
   if (MODE == LAT_INV_REAL) {
     T* out = static_cast<T*>(a.out);
-    for (int e = tid; e < n_el; e += nt) {
-      const int row = e >> logTP, c = e & (TP - 1);
-      const size_t gi = base + size_t(row) * M + 2 * c;
-      const V v = buf[prow(row) * TP + c];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      if (i >= ept) break;
+      const int e = tid + i * nt;
+      const V v = buf[sidx(e)];
       RP r;
       r.x = v.a.x * nrm;
       r.y = v.b.x * nrm;
-      *reinterpret_cast<RP*>(out + gi) = r;
+      *reinterpret_cast<RP*>(out + gidx(e)) = r;
     }
     return;
   }
-  // LAT_UPDATE
+  // LAT_UPDATE, in two batches of four elements: loads of the iterates first
   double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
   bool bad = false;
   const T sg = nrm * a.inv_L;
-  for (int e = tid; e < n_el; e += nt) {
-    const int row = e >> logTP, c = e & (TP - 1);
-    const size_t gi = base + size_t(row) * M + 2 * c;
-    const int n0 = int((m_first + 2 * c) & size_t(a.nz - 1));
-    const V g = escale(buf[prow(row) * TP + c], sg);        // g^k = (1/L) A^H(A eta - s)
-    const V z1 = *reinterpret_cast<const V*>(a.z1 + gi);
-    const V z2 = *reinterpret_cast<const V*>(a.z2 + gi);
-    const V eta = eadd(z1, escale(esub(z1, z2), a.mu_prev));
-    const T tau0 = a.w ? a.lam_over_L * a.w[n0] : a.lam_over_L;
-    const T tau1 = a.w ? a.lam_over_L * a.w[n0 + 1] : a.lam_over_L;
-    V z;
-    z.a = soft_threshold(csub(eta.a, g.a), tau0);
-    z.b = soft_threshold(csub(eta.b, g.b), tau1);
-    *reinterpret_cast<V*>(a.zout + gi) = z;
-    buf[prow(row) * TP + c] = eadd(z, escale(esub(z, z1), a.mu));
-    if (a.partial) {
-      const V d = esub(z, eta);
-      const V dg = eadd(d, g);
-      acc0 += double(d.a.x) * d.a.x + double(d.a.y) * d.a.y + double(d.b.x) * d.b.x +
-              double(d.b.y) * d.b.y;
-      acc1 += double(g.a.x) * g.a.x + double(g.a.y) * g.a.y + double(g.b.x) * g.b.x +
-              double(g.b.y) * g.b.y;
-      acc2 += double(dg.a.x) * dg.a.x + double(dg.a.y) * dg.a.y + double(dg.b.x) * dg.b.x +
-              double(dg.b.y) * dg.b.y;
+#pragma unroll
+  for (int h = 0; h < 8; h += 4) {
+    V z1v[4], z2v[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (h + i >= ept) break;
+      const size_t gi = gidx(tid + (h + i) * nt);
+      z1v[i] = *reinterpret_cast<const V*>(a.z1 + gi);
+      z2v[i] = *reinterpret_cast<const V*>(a.z2 + gi);
     }
-    bad |= !(isfinite(z.a.x) && isfinite(z.a.y) && isfinite(z.b.x) && isfinite(z.b.y));
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (h + i >= ept) break;
+      const int e = tid + (h + i) * nt;
+      const size_t gi = gidx(e);
+      const int n0 = int((m_first + 2 * (e & (TP - 1))) & size_t(a.nz - 1));
+      const V g = escale(buf[sidx(e)], sg);                 // g^k = (1/L) A^H(A eta - s)
+      const V z1 = z1v[i];
+      const V eta = eadd(z1, escale(esub(z1, z2v[i]), a.mu_prev));
+      const T tau0 = a.w ? a.lam_over_L * a.w[n0] : a.lam_over_L;
+      const T tau1 = a.w ? a.lam_over_L * a.w[n0 + 1] : a.lam_over_L;
+      V z;
+      z.a = soft_threshold(csub(eta.a, g.a), tau0);
+      z.b = soft_threshold(csub(eta.b, g.b), tau1);
+      *reinterpret_cast<V*>(a.zout + gi) = z;
+      buf[sidx(e)] = eadd(z, escale(esub(z, z1), a.mu));
+      if (a.partial) {
+        const V d = esub(z, eta);
+        const V dg = eadd(d, g);
+        acc0 += double(d.a.x) * d.a.x + double(d.a.y) * d.a.y + double(d.b.x) * d.b.x +
+                double(d.b.y) * d.b.y;
+        acc1 += double(g.a.x) * g.a.x + double(g.a.y) * g.a.y + double(g.b.x) * g.b.x +
+                double(g.b.y) * g.b.y;
+        acc2 += double(dg.a.x) * dg.a.x + double(dg.a.y) * dg.a.y + double(dg.b.x) * dg.b.x +
+                double(dg.b.y) * dg.b.y;
+      }
+      bad |= !(isfinite(z.a.x) && isfinite(z.a.y) && isfinite(z.b.x) && isfinite(z.b.y));
+    }
   }
   if (bad) atomicOr(a.flag, 1);
   __syncthreads();
   fft_smem<-1, false, T>(buf, TP, col, b, L, a.logL, tw, true);
   C* out = static_cast<C*>(a.out);
-  for (int e = tid; e < n_el; e += nt) {
-    const int row = e >> logTP, c = e & (TP - 1);
-    const size_t gi = base + size_t(row) * M + 2 * c;
-    *reinterpret_cast<V*>(out + gi) = escale(buf[prow(row) * TP + c], nrm);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    if (i >= ept) break;
+    const int e = tid + i * nt;
+    *reinterpret_cast<V*>(out + gidx(e)) = escale(buf[sidx(e)], nrm);
   }
   if (a.partial != nullptr) {
     __shared__ double red[3][32];
