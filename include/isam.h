@@ -72,7 +72,13 @@ typedef struct {
   int32_t precision;   /* ISAM_FP32 or ISAM_FP64                                    */
   int32_t nufft_J;     /* interpolation neighbours: 4, 6 or 8 (0: 6)               */
   int32_t nufft_os;    /* oversampling factor: 2 (0: 2)                            */
+  int32_t flags;       /* ISAM_FLAG_* bits (0: defaults)                          */
 } isam_params;
+
+/* Stolt positions and spectral phases depend on (|q|, k) only; by default a
+ * plan tabulates them when the table takes at most 64 MiB (B-scans) and the
+ * kernels evaluate them otherwise (volumes).  This flag forces evaluation. */
+#define ISAM_FLAG_NO_STOLT_TABLE 1
 
 typedef struct isam_plan isam_plan;
 

@@ -27,9 +27,16 @@ struct StoltConst {
   int focus;      // z0 != 0
 };
 
+// Stolt position and spectral phase of one (|q|, k_j) sample (mfl == INT_MIN:
+// evanescent).  Tabulated per plan when the table is small (B-scans).
+template <typename T> struct StoltEntry;
+template <> struct alignas(16) StoltEntry<float> { int mfl; float frac; float2 ph; };
+template <> struct alignas(16) StoltEntry<double> { int mfl; int pad; double frac; double2 ph; };
+
 template <typename T> struct Tables {
   T* scale = nullptr;        // [nz]  s(n - nz/2) / sqrt(nz)
   cplx<T>* disp = nullptr;   // [nk]  e^{j phi(k_j)}
+  StoltEntry<T>* stab = nullptr;  // [(ny/2+1)(nx/2+1)][nk] or null (computed on the fly)
 };
 
 // Min-max coefficients as polynomials in the fractional offset f.  With
@@ -94,6 +101,10 @@ template <typename T> cudaError_t launch_ax_fwd(const AxArgs<T>& a, int npairs, 
 template <typename T> cudaError_t launch_ax_adj(const AxArgs<T>& a, int npairs, cudaStream_t s);
 template <typename T> cudaError_t launch_ax_fused(const AxArgs<T>& a, int npairs, cudaStream_t s);
 template <typename T> size_t ax_smem_bytes(int K, int nk, bool adj);
+
+// Stolt table: entry [(|my| (nx/2+1) + |mx|) nk + j] for every |q| class
+template <typename T> cudaError_t launch_stolt_table(const AxArgs<T>& a, StoltEntry<T>* out,
+                                                     cudaStream_t s);
 
 // FP64 exact min-max coefficients at offsets f[0..n) (device), out[i*J + l]
 cudaError_t minmax_nodes(int nz, int K, int J, const double* f, int n, double* out,

@@ -71,6 +71,9 @@ struct isam_plan {
 namespace {
 
 constexpr int RED_BLOCKS = 1024;
+// Stolt position/phase tables are kept when at most this large (B-scans);
+// larger geometries (volumes) evaluate positions in the kernels.
+constexpr size_t kStoltTableMaxBytes = size_t(64) << 20;
 // power iteration used when the caller gives no L: the top eigenvalues of
 // A^H A lie close together, so convergence takes hundreds of steps
 constexpr int kPowerIters = 1000;
@@ -144,7 +147,7 @@ template <typename T> isam_status dalloc(T** p, size_t n) {
 }
 
 template <typename T> void impl_free(Impl<T>& im) {
-  cudaFree(im.tab.scale); cudaFree(im.tab.disp);
+  cudaFree(im.tab.scale); cudaFree(im.tab.disp); cudaFree(im.tab.stab);
   cudaFree(im.eta_hat); cudaFree(im.spec); cudaFree(im.grad); cudaFree(im.sdh);
   cudaFree(im.zA); cudaFree(im.zB); cudaFree(im.s_tmp);
   cudaFree(im.s_host_stage); cudaFree(im.out_stage);
@@ -188,6 +191,18 @@ template <typename T> isam_status impl_init(isam_plan* P, Impl<T>& im) {
     }
     ISAM_TRY(dalloc(&im.tab.disp, P->nk));
     CUDA_TRY(cudaMemcpy(im.tab.disp, h.data(), sizeof(cplx<T>) * P->nk, cudaMemcpyHostToDevice));
+  }
+  // Stolt positions and phases per |q| class, when the table is small
+  {
+    const size_t rows = size_t(P->ny / 2 + 1) * (P->nx / 2 + 1);
+    const size_t bytes = rows * P->nk * sizeof(StoltEntry<T>);
+    if (bytes <= kStoltTableMaxBytes && !(p.flags & ISAM_FLAG_NO_STOLT_TABLE)) {
+      ISAM_TRY(dalloc(&im.tab.stab, rows * P->nk));
+      AxArgs<T> a{};
+      a.sc = P->sc;
+      a.tab = im.tab;
+      CUDA_TRY(launch_stolt_table<T>(a, im.tab.stab, P->stream));
+    }
   }
   ISAM_TRY(dalloc(&im.eta_hat, P->n_img));
   ISAM_TRY(dalloc(&im.spec, P->n_spec));
@@ -501,6 +516,7 @@ isam_status validate(const isam_params* p) {
   const int os = p->nufft_os ? p->nufft_os : 2;
   if (os != 2) return ISAM_ERR_UNSUPPORTED;
   if (!isfinite(p->z0)) return ISAM_ERR_INVALID;
+  if (p->flags & ~ISAM_FLAG_NO_STOLT_TABLE) return ISAM_ERR_INVALID;
   for (int i = 0; i < 4; ++i)
     if (!isfinite(p->disp[i])) return ISAM_ERR_INVALID;
   return ISAM_OK;

@@ -108,6 +108,35 @@ __device__ __forceinline__ cplx<T> spectral_phase(const StoltConst& sc, const cp
   return ph;
 }
 
+// Row of the Stolt table for lateral frequency (mx, my) (rows by |mx|, |my|).
+__device__ __forceinline__ int stolt_class(const StoltConst& sc, int mx, int my) {
+  return abs(my) * (sc.nx / 2 + 1) + abs(mx);
+}
+
+// Stolt position and spectral phase of sample j of one column pair, from the
+// plan's table when present, else evaluated (float-float / double).
+template <typename T> struct Positions {
+  StoltPos<T> sp;
+  const StoltEntry<T>* row;
+  __device__ Positions(const AxArgs<T>& A, int mx, int my) : sp(A.sc, mx, my) {
+    row = A.tab.stab ? A.tab.stab + size_t(stolt_class(A.sc, mx, my)) * A.sc.nk : nullptr;
+  }
+  __device__ __forceinline__ bool at(const AxArgs<T>& A, int j, int& mfl, T& frac,
+                                     cplx<T>& ph) const {
+    if (row) {
+      const StoltEntry<T> e = row[j];
+      mfl = e.mfl;
+      frac = e.frac;
+      ph = e.ph;
+      return e.mfl != INT_MIN;
+    }
+    T turn;
+    if (!sp.at(A.sc, j, mfl, frac, turn)) return false;
+    ph = spectral_phase<T>(A.sc, A.tab.disp, j, turn);
+    return true;
+  }
+};
+
 // all J coefficients c_l(f)
 template <typename T, int J>
 __device__ __forceinline__ void coefficients(const Poly<T>& P, T frac, T* c) {
@@ -328,18 +357,18 @@ __global__ void __launch_bounds__(512) k_ax_fwd(const __grid_constant__ AxArgs<T
   build_twiddles<T>(tw, K, sc.logK);
   load_and_fft(A, Y, tw, c1, c2, two);
 
-  const StoltPos<T> sp(sc, mx, my);
+  const Positions<T> pos(A, mx, my);
   C* o1 = A.out + size_t(c1) * nk;
   C* o2 = A.out + size_t(c2) * nk;
   for (int j = threadIdx.x; j < nk; j += blockDim.x) {
     int mfl;
-    T frac, turn;
+    T frac;
+    C ph;
     C a1 = mk<T>(0, 0), a2 = mk<T>(0, 0);
-    if (sp.at(sc, j, mfl, frac, turn)) {
+    if (pos.at(A, j, mfl, frac, ph)) {
       T c[J];
       coefficients<T, J>(A.poly, frac, c);
       interp_pair<T, J>(Y, K, mfl, c, a1, a2);
-      const C ph = spectral_phase<T>(sc, A.tab.disp, j, turn);
       a1 = cmul(a1, ph);
       a2 = cmul(a2, ph);
     }
@@ -364,7 +393,7 @@ __global__ void __launch_bounds__(512, 2) k_ax_adj(const __grid_constant__ AxArg
   const bool two = c2 != c1;
   if (tid == 0) { ch_lo = INT_MAX; ch_hi = INT_MIN; }
   build_twiddles<T>(tw, K, sc.logK);
-  const StoltPos<T> sp(sc, mx, my);
+  const Positions<T> pos(A, mx, my);
   const C* r1 = A.in + size_t(c1) * nk;
   const C* r2 = A.in + size_t(c2) * nk;
   Sample<T> sm[NRES];
@@ -373,9 +402,9 @@ __global__ void __launch_bounds__(512, 2) k_ax_adj(const __grid_constant__ AxArg
     const int j = NRES * tid + rho;
     sm[rho].chunk = INT_MIN;
     int mfl;
-    T frac, turn;
-    if (j < nk && sp.at(sc, j, mfl, frac, turn)) {
-      const C ph = spectral_phase<T>(sc, A.tab.disp, j, turn);
+    T frac;
+    C ph;
+    if (j < nk && pos.at(A, j, mfl, frac, ph)) {
       sm[rho].val.a = cmulc(r1[j], ph);
       sm[rho].val.b = two ? cmulc(r2[j], ph) : mk<T>(0, 0);
       sm[rho].frac = frac;
@@ -423,7 +452,7 @@ __global__ void __launch_bounds__(512, 2) k_ax_fused(const __grid_constant__ AxA
   build_twiddles<T>(tw, K, sc.logK);
   load_and_fft(A, Y, tw, c1, c2, two);
 
-  const StoltPos<T> sp(sc, mx, my);
+  const Positions<T> pos(A, mx, my);
   Sample<T> sm[NRES];
   double rr = 0.0;
 #pragma unroll
@@ -433,14 +462,13 @@ __global__ void __launch_bounds__(512, 2) k_ax_fused(const __grid_constant__ AxA
     if (j >= nk) continue;
     const C dq = dqv[rho];
     int mfl;
-    T frac, turn;
+    T frac;
     C s1 = mk<T>(0, 0), s2 = mk<T>(0, 0), ph = mk<T>(0, 0);
-    const bool prop = sp.at(sc, j, mfl, frac, turn);
+    const bool prop = pos.at(A, j, mfl, frac, ph);
     if (prop) {
       T c[J];
       coefficients<T, J>(A.poly, frac, c);
       interp_pair<T, J>(Y, K, mfl, c, s1, s2);
-      ph = spectral_phase<T>(sc, A.tab.disp, j, turn);
       s1 = cmul(s1, ph);
       s2 = two ? cmul(s2, ph) : s1;
     }
@@ -473,6 +501,39 @@ __global__ void __launch_bounds__(512, 2) k_ax_fused(const __grid_constant__ AxA
   fft_smem<-1, false, T>(Y, 1, 0, tid, K, sc.logK, tw, true);
   store_columns(A, Y, c1, c2, two);
 }
+
+// One thread per (|q| class, k_j): the same evaluation the kernels do on the fly.
+template <typename T>
+__global__ void k_stolt_table(const __grid_constant__ AxArgs<T> A, StoltEntry<T>* out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int cls = blockIdx.y;
+  if (j >= A.sc.nk) return;
+  const int ncx = A.sc.nx / 2 + 1;
+  const int mx = cls % ncx, my = cls / ncx;
+  const StoltPos<T> sp(A.sc, mx, my);
+  StoltEntry<T> e{};
+  T turn;
+  if (sp.at(A.sc, j, e.mfl, e.frac, turn)) {
+    e.ph = spectral_phase<T>(A.sc, A.tab.disp, j, turn);
+  } else {
+    e.mfl = INT_MIN;
+    e.frac = T(0);
+    e.ph = mk<T>(0, 0);
+  }
+  out[size_t(cls) * A.sc.nk + j] = e;
+}
+
+template <typename T> cudaError_t launch_stolt_table(const AxArgs<T>& a, StoltEntry<T>* out,
+                                                     cudaStream_t s) {
+  const int rows = (a.sc.ny / 2 + 1) * (a.sc.nx / 2 + 1);
+  dim3 grid((a.sc.nk + 255) / 256, rows);
+  AxArgs<T> b = a;
+  b.tab.stab = nullptr;
+  k_stolt_table<T><<<grid, 256, 0, s>>>(b, out);
+  return cudaGetLastError();
+}
+template cudaError_t launch_stolt_table<float>(const AxArgs<float>&, StoltEntry<float>*, cudaStream_t);
+template cudaError_t launch_stolt_table<double>(const AxArgs<double>&, StoltEntry<double>*, cudaStream_t);
 
 template <typename T> size_t ax_smem_bytes(int K, int nk, bool adj) {
   (void)nk;

@@ -22,6 +22,7 @@ if not os.path.exists(LIB_PATH):
 _lib = ctypes.CDLL(LIB_PATH)
 
 ISAM_FP32, ISAM_FP64 = 0, 1
+ISAM_FLAG_NO_STOLT_TABLE = 1
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "CUDA error",
           4: "non-finite value in the solve", 5: "device wait timed out",
           6: "unsupported size or option"}
@@ -33,7 +34,8 @@ class IsamParams(ctypes.Structure):
                 ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("na", ctypes.c_double),
                 ("z0", ctypes.c_double), ("n_disp", ctypes.c_int32),
                 ("disp", ctypes.c_double * 4), ("precision", ctypes.c_int32),
-                ("nufft_J", ctypes.c_int32), ("nufft_os", ctypes.c_int32)]
+                ("nufft_J", ctypes.c_int32), ("nufft_os", ctypes.c_int32),
+                ("flags", ctypes.c_int32)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -95,7 +97,7 @@ def lib() -> ctypes.CDLL:
     return _lib
 
 
-def make_params(geom, precision: str = "fp32", J: int = 6) -> IsamParams:
+def make_params(geom, precision: str = "fp32", J: int = 6, stolt_table: bool = True) -> IsamParams:
     p = IsamParams()
     p.nx, p.ny, p.nk, p.nz = int(geom.nx), int(geom.ny), int(geom.nk), int(geom.nz or geom.nk)
     p.k_min, p.k_max = float(geom.k_min), float(geom.k_max)
@@ -108,6 +110,7 @@ def make_params(geom, precision: str = "fp32", J: int = 6) -> IsamParams:
     p.precision = ISAM_FP64 if precision == "fp64" else ISAM_FP32
     p.nufft_J = int(J)
     p.nufft_os = 2
+    p.flags = 0 if stolt_table else ISAM_FLAG_NO_STOLT_TABLE
     return p
 
 
@@ -120,7 +123,8 @@ def _stream_handle(stream) -> int:
 class Plan:
     """A plan for one geometry: isam_plan_create / isam_forward / isam_adjoint / isam_solve."""
 
-    def __init__(self, geom, precision: str = "fp32", J: int = 6, stream=None):
+    def __init__(self, geom, precision: str = "fp32", J: int = 6, stream=None,
+                 stolt_table: bool = True):
         import torch
         self.geom = geom
         self.precision = precision
@@ -128,7 +132,7 @@ class Plan:
         self.cplx_dtype = torch.complex128 if precision == "fp64" else torch.complex64
         self.image_shape = (geom.ny, geom.nx, geom.nz or geom.nk)
         self.spec_shape = (geom.ny, geom.nx, geom.nk)
-        self._params = make_params(geom, precision, J)
+        self._params = make_params(geom, precision, J, stolt_table)
         h = _P()
         _check(_lib.isam_plan_create(ctypes.byref(self._params), _P(_stream_handle(stream)),
                                      ctypes.byref(h)), "isam_plan_create")

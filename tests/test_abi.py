@@ -53,6 +53,7 @@ int main(void) {
   printf("isam_solve_info %zu\n", sizeof(isam_solve_info));
   P(isam_params, k_min) P(isam_params, dx) P(isam_params, z0) P(isam_params, n_disp)
   P(isam_params, disp) P(isam_params, precision) P(isam_params, nufft_os)
+  P(isam_params, flags)
   P(isam_solve_opts, max_iter) P(isam_solve_opts, w_dev) P(isam_solve_opts, L)
   P(isam_solve_opts, eps) P(isam_solve_state, k) P(isam_solve_state, L)
   P(isam_solve_info, rr) P(isam_solve_info, status)
@@ -103,6 +104,7 @@ def _params(isam, **kw):
     ("nufft_J", 5, 6),
     ("nufft_os", 3, 6),
     ("precision", 7, 1),
+    ("flags", 2, 1),         # unknown flag bit
 ])
 def test_plan_create_rejects_bad_parameters_before_any_device_call(isam, field, value, status):
     lib = isam.lib()
