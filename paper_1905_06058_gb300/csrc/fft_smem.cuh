@@ -114,20 +114,20 @@ __device__ __forceinline__ void sincospi_(float x, float* s, float* c) { sincosp
 __device__ __forceinline__ void sincospi_(double x, double* s, double* c) { sincospi(x, s, c); }
 
 // Twiddle table of an L-point transform, in shared memory: for every pass
-// with span Ns > 1 and radix R, entries k (R-1) + (r-1) of that pass's
-// segment hold e^{-2 pi i r k / (Ns R)}, k < Ns, 1 <= r < R.  Threads with
-// consecutive k read consecutive (R-1)-entry rows: no bank conflicts.
+// with span Ns > 1 and radix R, entry k of that pass's segment holds
+// w_k = e^{-2 pi i k / (Ns R)}, k < Ns.  A butterfly raises w_k to the powers
+// r = 2 .. R-1 itself by repeated complex multiplication, so each pass reads
+// one table entry per butterfly instead of R - 1.
 __host__ __device__ __forceinline__ int twiddle_entries(int L, int logL) {
   if (L < 8) return 0;
   int n = 0, Ns = 1;
   const int n8 = logL / 3;
   for (int p = 0; p < n8; ++p) {
-    if (Ns > 1) n += Ns * 7;
+    if (Ns > 1) n += Ns;
     Ns *= 8;
   }
   const int rem = logL - 3 * n8;
-  if (rem == 2 && Ns > 1) n += Ns * 3;
-  if (rem == 1 && Ns > 1) n += Ns;
+  if (rem && Ns > 1) n += Ns;
   return n;
 }
 
@@ -144,14 +144,9 @@ __device__ __forceinline__ void build_twiddles(cplx<T>* tab, int L, int logL) {
         for (int k = threadIdx.x; k < Ns; k += blockDim.x) {
           T s, c;
           sincospi_(T(2 * k) / T(Ns * R), &s, &c);
-          const cplx<T> w1 = mk<T>(c, -s);
-          cplx<T> w = w1;
-          for (int r = 1; r < R; ++r) {
-            tab[off + k * (R - 1) + (r - 1)] = w;
-            w = cmul(w, w1);
-          }
+          tab[off + k] = mk<T>(c, -s);
         }
-        off += Ns * (R - 1);
+        off += Ns;
       }
       Ns *= R;
     }
@@ -193,10 +188,13 @@ __device__ __forceinline__ void stockham_pass(E* buf, int stride, int col, int b
       const int k = j & (Ns - 1);
       E* a = v + u * R;
       if (Ns > 1) {
+        cplx<T> w1 = tw[k];
+        if (SIGN > 0) w1.y = -w1.y;
+        cplx<T> w = w1;
+        a[1] = emul(a[1], w);
 #pragma unroll
-        for (int r = 1; r < R; ++r) {
-          cplx<T> w = tw[k * (R - 1) + (r - 1)];
-          if (SIGN > 0) w.y = -w.y;
+        for (int r = 2; r < R; ++r) {
+          w = cmul(w, w1);
           a[r] = emul(a[r], w);
         }
       }
@@ -227,7 +225,7 @@ __device__ __forceinline__ void fft_smem(E* buf, int stride, int col, int b, int
         stockham_pass<SIGN, 8, true, T>(buf, stride, col, b, L, Ns, tw, active);
       else
         stockham_pass<SIGN, 8, false, T>(buf, stride, col, b, L, Ns, tw, active);
-      if (Ns > 1) tw += Ns * 7;
+      if (Ns > 1) tw += Ns;
       Ns *= 8;
     }
     const int rem = logL - 3 * n8;

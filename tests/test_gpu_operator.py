@@ -54,6 +54,11 @@ CASES = [
     ("volume_8x8x64_nz128", dict(nx=8, ny=8, nk=64, nz=128)),
     ("evanescent_edge", dict(nx=32, nk=64, nz=64, dx_scale=0.08)),
     ("no_focus_no_disp", dict(nx=32, nk=64, nz=64, dispersion=False, focus_frac=0.5)),
+    # nz = 2048 (K = 4096, 512 threads per column pair): the benchmarked size
+    ("bscan_8x2048", dict(nx=8, nk=2048, nz=2048)),
+    ("ascan_q0_2048", dict(nx=1, nk=2048, nz=2048)),
+    ("volume_4x2x2048", dict(nx=4, ny=2, nk=2048, nz=2048)),
+    ("bscan_4x1024_nz2048", dict(nx=4, nk=1024, nz=2048)),
 ]
 
 
@@ -74,6 +79,21 @@ def test_forward_adjoint_match_oracle(torch, prec, name, kw, table):
     a_ref = ref.adjoint(y)
     assert rel(a, a_ref) < TOL[prec], "adjoint"
     plan.close()
+
+
+@pytest.mark.parametrize("J", [4, 6, 8])
+def test_k4096_matches_oracle_for_every_J(torch, J):
+    """nz = 2048 (K = 4096) at 16 lateral columns, FP32, against the oracle."""
+    wl = I.small_bscan(nx=16, nk=2048, nz=2048, seed=11)
+    ref = O.IsamOracle(wl.geom, "nufft", J=J)
+    eta = I.random_image(ref.image_shape, 12)
+    y = I.random_spectra(ref.spec_shape, 13)
+    plan = plan_for(wl.geom, "fp32", J=J)
+    s = plan.forward(to_dev(torch, eta, "fp32", True)).cpu().numpy()
+    a = plan.adjoint(to_dev(torch, y, "fp32", False)).cpu().numpy()
+    plan.close()
+    assert rel(s, ref.forward(eta)) < 1e-5
+    assert rel(a, ref.adjoint(y)) < 1e-5
 
 
 @pytest.mark.parametrize("J", [4, 8])

@@ -55,6 +55,21 @@ def test_fista_matches_oracle(torch, prec, tol, table):
     plan.close()
 
 
+def test_fista_nz2048_matches_oracle(torch):
+    """nz = 2048 (K = 4096, the benchmarked launch shape of the fused gradient
+    kernel), with the stop rule's partial norms, against the oracle's FISTA."""
+    from paper_1905_06058_gb300.isam import Plan
+    wl, ref, s, L = problem(nx=8, nk=2048, nz=2048, seed=21, n_points=12)
+    lam = O.lambda_from_data(ref.adjoint, s, 0.05)
+    res = O.fista(ref.forward, ref.adjoint, s, lam, L, max_iter=30, shape=ref.image_shape)
+    plan = Plan(wl.geom)
+    out, info = plan.solve(dev(torch, s, np.float32), lambda_abs=lam, L=L, max_iter=30,
+                           tol=1e-30, check_every=5)
+    assert info["iterations"] == 30
+    assert rel(out.cpu().numpy(), res.eta) < 1e-3
+    plan.close()
+
+
 def test_weighted_addback_and_lambda_rule(torch):
     """MBIR+ (depth weights 0.5 -> 1, residual added back, §3.1, §4.2)."""
     from paper_1905_06058_gb300.isam import Plan
