@@ -19,7 +19,12 @@ What it computes (paper section / equation in brackets):
 * adjoint  A^H y = K_hat^H y under the real inner product  [Eq. 17];
 * weighted complex soft threshold [Eq. 14], relative residual [Eq. 15],
   FISTA [Alg. 1], residual add-back [Alg. 1, optional last step];
-* Lipschitz constant of the gradient by power iteration.
+* Lipschitz constant of the gradient by power iteration;
+* derivatives for calibrating the dispersion coefficients a_1..a_4 (Eq. 7)
+  and the focal depth z0 by gradient descent: <dA/dtheta x, y>, the
+  Jacobian-transpose of the soft threshold (Eq. 14), and the gradient of
+  <z_bar, z^K> through K unrolled FISTA iterations (Alg. 1) with lambda and
+  L held fixed.
 
 Readings of points the paper leaves open (they are the same on the CUDA
 side, implemented independently):
@@ -467,3 +472,108 @@ def dispersion_compensated_ifft(g, s_d: np.ndarray) -> np.ndarray:
     E = np.exp(-1j * (np.outer(gr.z, 2 * gr.k)))          # [nz, nk]
     a = s_d * np.exp(-1j * phi)
     return np.einsum("zk,...k->...z", E, a) / math.sqrt(gr.nz)
+
+
+# ----------------------------------------------------------------------------
+# Calibration derivatives: theta = (a1, a2, a3, a4, z0)
+# ----------------------------------------------------------------------------
+# A depends on theta only through the spectral phase P(q, k) = e^{j phi(k)}
+# e^{j (2k + beta) z0} [Eq. 7, Eq. 13 and the focus reading], so
+#   dA/dtheta x = Re F^{-1}( j D_theta . P . N(F x) ),
+#   D_{a_i} = (k - k0)^i,   D_{z0} = 2k + beta   (0 on evanescent samples).
+
+PARAM_NAMES = ("a1", "a2", "a3", "a4", "z0")
+
+
+def phase_log_derivatives(g, grid: Grid) -> np.ndarray:
+    """D_theta(q, k), [5, ny, nx, nk]: dP/dtheta = j D_theta P  [Eq. 7, 13]."""
+    beta, prop = stolt_beta(grid.q2[..., None], grid.k[None, None, :])
+    shape = beta.shape
+    D = np.zeros((5,) + shape)
+    d = grid.k - grid.k0
+    for i in range(4):
+        D[i] = np.broadcast_to(d ** (i + 1), shape)
+    D[4] = np.where(prop, 2 * grid.k[None, None, :] + beta, 0.0)
+    return D
+
+
+def forward_param_derivative(op: IsamOracle, x: np.ndarray, i: int) -> np.ndarray:
+    """dA/dtheta_i x: the forward model with j D_i inserted after the phase."""
+    D = phase_log_derivatives(op.g, op.grid)[i]
+    S = 1j * D * op.phase * op.axial_forward(lateral_fft(x))
+    return lateral_ifft(S).real
+
+
+def param_grad(op: IsamOracle, x: np.ndarray, y: np.ndarray) -> np.ndarray:
+    """<dA/dtheta x, y> for the five parameters (real inner product on spectra)."""
+    return np.array([float(np.sum(forward_param_derivative(op, x, i) * y)) for i in range(5)])
+
+
+def soft_threshold_vjp(u: np.ndarray, tau, zbar: np.ndarray) -> np.ndarray:
+    """J^T zbar for z = T_tau(u) of Eq. 14, u complex (a map on R^2 per element).
+
+    Where |u| > tau, T(u) = u - tau u/|u| and its (symmetric) Jacobian applied
+    to v is v - tau (v/|u| - u Re(conj(u) v)/|u|^3); where |u| <= tau, T = 0.
+    """
+    a = np.abs(u)
+    live = a > tau
+    tau = np.broadcast_to(tau, u.shape)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        inv = np.where(live, 1.0 / np.where(live, a, 1.0), 0.0)
+        v = zbar - tau * (zbar * inv - u * np.real(np.conj(u) * zbar) * inv ** 3)
+    return np.where(live, v, 0.0)
+
+
+@dataclass
+class UnrolledGrad:
+    z: np.ndarray            # z^K
+    theta_bar: np.ndarray    # d<z_bar, z^K>/dtheta, [5]
+    s_bar: np.ndarray        # d<z_bar, z^K>/ds_d
+
+
+def fista_unrolled_vjp(op: IsamOracle, s_d: np.ndarray, lam: float, L: float, K: int,
+                       z_bar: np.ndarray, w=1.0) -> UnrolledGrad:
+    """Gradient of <z_bar, z^K> (real inner product) through K FISTA iterations.
+
+    Forward (Alg. 1 with step 1/L, threshold lambda w / L, t^1 = 1):
+      eta^k = z^{k-1} + mu_{k-1} (z^{k-1} - z^{k-2}),  mu_{k-1} = (t^{k-1}-1)/t^k,
+      u^k = eta^k - (1/L) A^H (A eta^k - s_d),  z^k = T(u^k),  z^0 = z^{-1} = 0.
+    Reverse, k = K .. 1 (every iterate kept; lambda and L are constants):
+      ubar = J_T(u^k)^T zbar^k,  etabar = ubar - (1/L) A^H A ubar,
+      theta_bar -= (1/L) (<dA ubar, A eta^k - s_d> + <A ubar, dA eta^k>),
+      s_bar += (1/L) A ubar,
+      zbar^{k-1} += (1 + mu_{k-1}) etabar,  zbar^{k-2} -= mu_{k-1} etabar.
+    """
+    shape = op.image_shape
+    zero = np.zeros(shape, np.complex128)
+    tau = lam * w / L
+    t = fista_t_sequence(K + 1)           # t[k-1] = t^k
+    mu = np.zeros(K + 1)                  # mu[k] = (t^k - 1)/t^{k+1}, mu[0] = 0
+    for k in range(1, K + 1):
+        mu[k] = (t[k - 1] - 1) / t[k]
+    z_prev2, z_prev = zero, zero
+    etas, us = [None], [None]
+    for k in range(1, K + 1):
+        eta = z_prev + mu[k - 1] * (z_prev - z_prev2)
+        u = eta - op.adjoint(op.forward(eta) - s_d) / L
+        etas.append(eta)
+        us.append(u)
+        z_prev2, z_prev = z_prev, soft_threshold(u, tau)
+    zK = z_prev
+    zbar = [zero.copy() for _ in range(K + 1)]
+    zbar[K] = z_bar.astype(np.complex128)
+    theta_bar = np.zeros(5)
+    s_bar = np.zeros(op.spec_shape)
+    for k in range(K, 0, -1):
+        ubar = soft_threshold_vjp(us[k], tau, zbar[k])
+        Au = op.forward(ubar)
+        etabar = ubar - op.adjoint(Au) / L
+        r = op.forward(etas[k]) - s_d
+        theta_bar -= (param_grad(op, ubar, r) + param_grad(op, etas[k], Au)) / L
+        s_bar += Au / L
+        if k - 1 >= 1:
+            zbar[k - 1] += (1 + mu[k - 1]) * etabar
+        if k - 2 >= 1:
+            zbar[k - 2] -= mu[k - 1] * etabar
+    return UnrolledGrad(zK, theta_bar, s_bar)
+
