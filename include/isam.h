@@ -165,6 +165,54 @@ isam_status isam_max_abs(isam_plan* plan, const void* eta, double* out);
 isam_status isam_max_abs_noalloc(const void* x, int64_t n, int32_t precision, double* out,
                                  void* stream);
 
+/* ---- Calibration of the dispersion coefficients and the focal depth -------
+ * The paper notes that a (Eq. 7) may be found by an autofocus method (§2)
+ * and places the focus at a known depth; here theta = (a_1, a_2, a_3, a_4, z0)
+ * can instead be fitted by gradient descent through the model.  A depends on
+ * theta only through the spectral phase e^{j phi(k)} e^{j (2k + beta) z0}, so
+ *   dA/dtheta x = Re F^{-1}( j D_theta . e^{j phi} e^{j(2k+beta)z0} . N(F x) ),
+ *   D_{a_i} = (k - k0)^i,  D_{z0} = 2k + beta  (zero on evanescent samples).
+ * Derivatives are taken with respect to a_i in rad m^i and z0 in m. */
+#define ISAM_N_PARAMS 5
+
+/* Replace theta of an existing plan (a_1..a_{n_disp}; the rest become 0):
+ * rebuilds the phase and Stolt tables and forgets the cached L (||A||^2
+ * depends on phi).  Synchronous.  Other tables and workspace are kept. */
+isam_status isam_set_model(isam_plan* plan, int32_t n_disp, const double* disp, double z0);
+
+/* grad[i] = <dA/dtheta_i x, y> (real inner product on spectra), i < 5: the
+ * gradient of <A x, y> with respect to theta.  x: device image, y: device
+ * spectra; grad: host double[ISAM_N_PARAMS].  Sums in FP64.  Synchronous. */
+isam_status isam_param_grad(isam_plan* plan, const void* x, const void* y, double* grad);
+
+/* Unrolled FISTA with checkpoints, for differentiating the reconstruction:
+ * K = opts->max_iter iterations of Alg. 1 from z^0 = 0 with lambda =
+ * opts->lambda_abs (> 0) and step 1/opts->L (> 0) held fixed, no stop rule,
+ * no add-back (ISAM_ERR_INVALID otherwise), weights opts->w_dev.  Writes z^K
+ * to z_out and, if ckpt is not NULL, the pair (z^{c e}, z^{c e - 1}) before
+ * iteration c e + 1 to images 2c, 2c+1 of ckpt, e = every; ckpt holds
+ * isam_unrolled_checkpoint_images(K, every) images of the plan's type.
+ * Synchronous; ISAM_ERR_NONFINITE if an iterate is not finite. */
+int32_t isam_unrolled_checkpoint_images(int32_t K, int32_t every);
+isam_status isam_fista_unrolled(isam_plan* plan, const void* s_d, const isam_solve_opts* opts,
+                                int32_t every, void* ckpt, void* z_out);
+
+/* Gradient of <z_bar, z^K> (real inner product) through the iterations of
+ * isam_fista_unrolled (same s_d, opts, every and the ckpt it wrote, theta
+ * unchanged since): grad (host double[5]) with respect to theta and, when
+ * s_bar (device spectra) is not NULL, with respect to s_d.  Each segment of
+ * `every` iterations is recomputed from its checkpoint, then reversed:
+ *   ubar = J_T(u^k)^T zbar^k   (Jacobian of the soft threshold, Eq. 14),
+ *   etabar = ubar - (1/L) A^H A ubar,
+ *   grad -= (1/L)(<dA ubar, A eta^k - s_d> + <A ubar, dA eta^k>),
+ *   s_bar += (1/L) A ubar,
+ *   zbar^{k-1} += (1 + mu_{k-1}) etabar,  zbar^{k-2} -= mu_{k-1} etabar.
+ * Workspace: 2 every + 8 images and two spectra, kept by the plan.  Synchronous. */
+isam_status isam_fista_unrolled_vjp(isam_plan* plan, const void* s_d,
+                                    const isam_solve_opts* opts, int32_t every,
+                                    const void* ckpt, const void* z_bar, void* s_bar,
+                                    double* grad);
+
 /* Kernel launches issued by the last isam_forward / isam_adjoint / isam_solve. */
 int64_t isam_last_launch_count(const isam_plan* plan);
 

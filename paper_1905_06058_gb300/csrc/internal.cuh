@@ -78,6 +78,7 @@ template <typename T> struct LatArgs {
   T inv_L, lam_over_L, mu_prev, mu;
   double* partial;       // [gridDim.x*gridDim.y][3] norm partials, or null
   int* flag;             // non-finite flag
+  cplx<T>* uout;         // optional: u^k = eta^k - g^k before the threshold
 };
 
 // Columns q and -q share the Stolt map; the axial kernels process them as a
@@ -129,6 +130,26 @@ template <typename T> cudaError_t launch_rsub(const T* a, const T* b, T* y, size
                                                cudaStream_t s);
 template <typename T> cudaError_t launch_caxpy(const cplx<T>* x, const cplx<T>* v, T alpha,
                                                 cplx<T>* y, size_t n, cudaStream_t s);
+
+// calibration (k_calib.cu): <dA/dtheta x, y> partial sums per column pair
+template <typename T> struct ParamArgs {
+  cplx<T>* su;           // S_x [ny][nx][nk]; overwritten by (S(q) + conj S(-q))/2 if write_fa
+  const cplx<T>* se;     // S_eta of a second model spectrum, or null
+  const cplx<T>* fd;     // lateral spectrum of data (all columns), or null
+  T fd_sign;             // data term: F1 = Re-spectrum(se) + fd_sign * fd
+  const int2* pairs;
+  StoltConst sc;
+  double* partial;       // [npairs][5], accumulated
+  int write_fa;
+};
+template <typename T> cudaError_t launch_param_reduce(const ParamArgs<T>& a, int npairs,
+                                                      cudaStream_t s);
+template <typename T> cudaError_t launch_st_vjp(const cplx<T>* u, const cplx<T>* zbar, const T* w,
+                                                T lam_over_L, int nz, cplx<T>* out, size_t n,
+                                                cudaStream_t s);
+template <typename T> cudaError_t launch_bwd_combine(const cplx<T>* ubar, const cplx<T>* b,
+                                                     T inv_L, T mu, cplx<T>* zb1, cplx<T>* zb2,
+                                                     size_t n, cudaStream_t s);
 
 int lat_tile(int L, int M);   // pair-columns per block of a lateral pass
 template <typename T> size_t lat_smem_bytes(int L, int TP);

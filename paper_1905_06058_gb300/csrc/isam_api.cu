@@ -34,6 +34,12 @@ template <typename T> struct Impl {
   T* s_tmp = nullptr;           // [ny][nx][nk]  real spectra temporary
   T* s_host_stage = nullptr;    // device copy of host s_d for isam_solve_host
   cplx<T>* out_stage = nullptr; // device image for isam_solve_host
+  // calibration: second complex spectrum, segment storage of the unrolled
+  // gradient (u^k and eta_hat^k of up to seg_cap iterations), adjoint images
+  cplx<T>* spec2 = nullptr;
+  cplx<T>* seg = nullptr;
+  int seg_cap = 0;
+  cplx<T>* cal = nullptr;       // [5][n_img]: zbar x 3, ubar, b
   bool ready = false;
 };
 
@@ -57,6 +63,7 @@ struct isam_plan {
   double* hscal = nullptr;      // pinned host mirror [8]
   int* flag = nullptr;          // device non-finite flag
   double L_cache = 0.0;
+  double* cpartial = nullptr;   // [npairs][5] calibration partial sums
   int64_t launches = 0;
   size_t n_img = 0, n_spec = 0;
   // opt-in per-kernel-class timing with CUDA events on the plan's stream
@@ -151,6 +158,7 @@ template <typename T> void impl_free(Impl<T>& im) {
   cudaFree(im.eta_hat); cudaFree(im.spec); cudaFree(im.grad); cudaFree(im.sdh);
   cudaFree(im.zA); cudaFree(im.zB); cudaFree(im.s_tmp);
   cudaFree(im.s_host_stage); cudaFree(im.out_stage);
+  cudaFree(im.spec2); cudaFree(im.seg); cudaFree(im.cal);
   im = Impl<T>();
 }
 
@@ -166,6 +174,38 @@ template <typename T> bool precision_fits(const isam_plan* P) {
          ax_smem_bytes<T>(P->K, P->nk, false) <= 227u * 1024u;
 }
 
+// Tables that depend on the dispersion coefficients and the focal depth:
+// e^{j phi(k_j)} (Eq. 7) and, when kept, the Stolt position/phase table.
+// Asynchronous on the plan's stream (the host vector is copied synchronously).
+template <typename T> isam_status phase_tables(isam_plan* P, Impl<T>& im) {
+  const isam_params& p = P->p;
+  {
+    std::vector<cplx<T>> h(P->nk);
+    const double dk = (p.k_max - p.k_min) / (P->nk - 1);
+    const double k0 = 0.5 * (p.k_min + p.k_max);
+    for (int j = 0; j < P->nk; ++j) {
+      const double d = (p.k_min + dk * j) - k0;
+      double phi = 0.0, pw = 1.0;
+      for (int i = 0; i < p.n_disp; ++i) { pw *= d; phi += p.disp[i] * pw; }
+      h[j] = mk<T>(T(cos(phi)), T(sin(phi)));
+    }
+    if (!im.tab.disp) ISAM_TRY(dalloc(&im.tab.disp, P->nk));
+    CUDA_TRY(cudaMemcpy(im.tab.disp, h.data(), sizeof(cplx<T>) * P->nk, cudaMemcpyHostToDevice));
+  }
+  {
+    const size_t rows = size_t(P->ny / 2 + 1) * (P->nx / 2 + 1);
+    const size_t bytes = rows * P->nk * sizeof(StoltEntry<T>);
+    if (bytes <= kStoltTableMaxBytes && !(p.flags & ISAM_FLAG_NO_STOLT_TABLE)) {
+      if (!im.tab.stab) ISAM_TRY(dalloc(&im.tab.stab, rows * P->nk));
+      AxArgs<T> a{};
+      a.sc = P->sc;
+      a.tab = im.tab;
+      CUDA_TRY(launch_stolt_table<T>(a, im.tab.stab, P->stream));
+    }
+  }
+  return ISAM_OK;
+}
+
 template <typename T> isam_status impl_init(isam_plan* P, Impl<T>& im) {
   if (im.ready) return ISAM_OK;
   if (!precision_fits<T>(P)) return ISAM_ERR_UNSUPPORTED;
@@ -178,32 +218,7 @@ template <typename T> isam_status impl_init(isam_plan* P, Impl<T>& im) {
     ISAM_TRY(dalloc(&im.tab.scale, P->nz));
     CUDA_TRY(cudaMemcpy(im.tab.scale, h.data(), sizeof(T) * P->nz, cudaMemcpyHostToDevice));
   }
-  // dispersion phase e^{j phi(k_j)}, phi = sum a_i (k - k0)^i  (Eq. 7)
-  {
-    std::vector<cplx<T>> h(P->nk);
-    const double dk = (p.k_max - p.k_min) / (P->nk - 1);
-    const double k0 = 0.5 * (p.k_min + p.k_max);
-    for (int j = 0; j < P->nk; ++j) {
-      const double d = (p.k_min + dk * j) - k0;
-      double phi = 0.0, pw = 1.0;
-      for (int i = 0; i < p.n_disp; ++i) { pw *= d; phi += p.disp[i] * pw; }
-      h[j] = mk<T>(T(cos(phi)), T(sin(phi)));
-    }
-    ISAM_TRY(dalloc(&im.tab.disp, P->nk));
-    CUDA_TRY(cudaMemcpy(im.tab.disp, h.data(), sizeof(cplx<T>) * P->nk, cudaMemcpyHostToDevice));
-  }
-  // Stolt positions and phases per |q| class, when the table is small
-  {
-    const size_t rows = size_t(P->ny / 2 + 1) * (P->nx / 2 + 1);
-    const size_t bytes = rows * P->nk * sizeof(StoltEntry<T>);
-    if (bytes <= kStoltTableMaxBytes && !(p.flags & ISAM_FLAG_NO_STOLT_TABLE)) {
-      ISAM_TRY(dalloc(&im.tab.stab, rows * P->nk));
-      AxArgs<T> a{};
-      a.sc = P->sc;
-      a.tab = im.tab;
-      CUDA_TRY(launch_stolt_table<T>(a, im.tab.stab, P->stream));
-    }
-  }
+  ISAM_TRY(phase_tables<T>(P, im));
   ISAM_TRY(dalloc(&im.eta_hat, P->n_img));
   ISAM_TRY(dalloc(&im.spec, P->n_spec));
   ISAM_TRY(dalloc(&im.grad, P->n_img));
@@ -347,23 +362,31 @@ template <typename T> isam_status power_iteration(isam_plan* P, int iters, doubl
 // ----------------------------------------------------------------------------
 // FISTA (Alg. 1)
 // ----------------------------------------------------------------------------
+// One iteration of Alg. 1: the fused gradient kernel on eta_hat^k (ehat_in,
+// default the plan's buffer), then the lateral update, which writes z^k to
+// zout, eta_hat^{k+1} to ehat_out (default the plan's buffer) and, when
+// u_out is given, u^k = eta^k - g^k (before the threshold).
 template <typename T> isam_status fista_iteration(isam_plan* P, Impl<T>& im,
                                                   const cplx<T>* z1, const cplx<T>* z2,
                                                   cplx<T>* zout, const T* w, double lam,
                                                   double L, double mu_prev, double mu,
-                                                  bool norms) {
+                                                  bool norms, const cplx<T>* ehat_in = nullptr,
+                                                  cplx<T>* ehat_out = nullptr,
+                                                  cplx<T>* u_out = nullptr) {
   cudaStream_t s = P->stream;
-  AxArgs<T> ax = ax_args<T>(P, im, im.eta_hat, im.grad);
+  if (!ehat_in) ehat_in = im.eta_hat;
+  if (!ehat_out) ehat_out = im.eta_hat;
+  AxArgs<T> ax = ax_args<T>(P, im, ehat_in, im.grad);
   ax.sdh = im.sdh;
   ISAM_TRY(launch(P, ISAM_KCLASS_AX_FUSED, [&] { return launch_ax_fused<T>(ax, P->npairs, s); }));
   LatArgs<T> u;
   if (P->ny == 1) {
-    u = lat_args<T>(1, P->nx, P->nz, im.grad, im.eta_hat);
+    u = lat_args<T>(1, P->nx, P->nz, im.grad, ehat_out);
   } else {
     ISAM_TRY(lat<T>(P, LAT_C2C_INV, lat_args<T>(P->ny, P->nx, P->nz, im.grad, im.grad)));
-    u = lat_args<T>(1, P->ny, P->nx * P->nz, im.grad, im.eta_hat);
+    u = lat_args<T>(1, P->ny, P->nx * P->nz, im.grad, ehat_out);
   }
-  u.z1 = z1; u.z2 = z2; u.zout = zout; u.w = w; u.nz = P->nz;
+  u.z1 = z1; u.z2 = z2; u.zout = zout; u.w = w; u.nz = P->nz; u.uout = u_out;
   u.inv_L = T(1.0 / L); u.lam_over_L = T(lam / L); u.mu_prev = T(mu_prev); u.mu = T(mu);
   u.partial = norms ? P->partial : nullptr;
   u.flag = P->flag;
@@ -373,7 +396,7 @@ template <typename T> isam_status fista_iteration(isam_plan* P, Impl<T>& im,
     ISAM_TRY(launch(P, ISAM_KCLASS_MISC, [&] { return launch_sum3(P->partial, nblk, P->dscal + 1, s); }));
   }
   if (P->ny > 1)
-    ISAM_TRY(lat<T>(P, LAT_C2C_FWD, lat_args<T>(P->ny, P->nx, P->nz, im.eta_hat, im.eta_hat)));
+    ISAM_TRY(lat<T>(P, LAT_C2C_FWD, lat_args<T>(P->ny, P->nx, P->nz, ehat_out, ehat_out)));
   return ISAM_OK;
 }
 
@@ -721,6 +744,7 @@ void isam_plan_destroy(isam_plan* P) {
   impl_free(P->f32);
   impl_free(P->f64);
   cudaFree(P->partial);
+  cudaFree(P->cpartial);
   cudaFree(P->pairs);
   cudaFree(P->dscal);
   cudaFree(P->flag);
@@ -854,6 +878,292 @@ isam_status isam_profile_read(isam_plan* P, double* ms, int64_t* counts, int32_t
     if (reset) { P->prof_ms[c] = 0.0; P->prof_n[c] = 0; }
   }
   return ISAM_OK;
+}
+
+}  // extern "C"
+
+// ----------------------------------------------------------------------------
+// Calibration of theta = (a_1..a_4, z0): parameter derivatives of A and the
+// gradient through unrolled FISTA iterations (lambda and L held fixed).
+// ----------------------------------------------------------------------------
+namespace {
+
+template <typename T> isam_status calib_buffers(isam_plan* P, Impl<T>& im, int seg_cap) {
+  if (!im.spec2) ISAM_TRY(dalloc(&im.spec2, P->n_spec));
+  if (!im.cal) ISAM_TRY(dalloc(&im.cal, 5 * P->n_img));
+  if (!P->cpartial) ISAM_TRY(dalloc(&P->cpartial, size_t(P->npairs) * 5));
+  if (seg_cap > im.seg_cap) {
+    cudaFree(im.seg);
+    im.seg = nullptr;
+    im.seg_cap = 0;
+    ISAM_TRY(dalloc(&im.seg, size_t(2 * seg_cap + 1) * P->n_img));
+    im.seg_cap = seg_cap;
+  }
+  if (!im.zA) ISAM_TRY(dalloc(&im.zA, P->n_img));
+  if (!im.zB) ISAM_TRY(dalloc(&im.zB, P->n_img));
+  if (!im.sdh) ISAM_TRY(dalloc(&im.sdh, P->n_spec));
+  if (!im.s_tmp) ISAM_TRY(dalloc(&im.s_tmp, P->n_spec));
+  return ISAM_OK;
+}
+
+// Sum the [npairs][5] partials in a fixed order and convert the moments to
+// derivatives: d/da_i = dk^i m_i, d/dz0 = dk m_z, times `factor`.
+isam_status read_param_partials(isam_plan* P, double factor, double* grad) {
+  std::vector<double> h(size_t(P->npairs) * 5);
+  CUDA_TRY(cudaMemcpyAsync(h.data(), P->cpartial, h.size() * sizeof(double),
+                           cudaMemcpyDeviceToHost, P->stream));
+  CUDA_TRY(cudaStreamSynchronize(P->stream));
+  harvest_events(P);
+  double m[5] = {0, 0, 0, 0, 0};
+  for (int b = 0; b < P->npairs; ++b)
+    for (int i = 0; i < 5; ++i) m[i] += h[size_t(b) * 5 + i];
+  const double dk = (P->p.k_max - P->p.k_min) / (P->nk - 1);
+  double pw = 1.0;
+  for (int i = 0; i < 4; ++i) {
+    pw *= dk;
+    grad[i] = factor * pw * m[i];
+  }
+  grad[4] = factor * dk * m[4];
+  return ISAM_OK;
+}
+
+template <typename T> ParamArgs<T> param_args(isam_plan* P, cplx<T>* su, const cplx<T>* se,
+                                              const cplx<T>* fd, T fd_sign, bool write_fa) {
+  ParamArgs<T> a{};
+  a.su = su; a.se = se; a.fd = fd; a.fd_sign = fd_sign;
+  a.pairs = P->pairs; a.sc = P->sc; a.partial = P->cpartial; a.write_fa = write_fa ? 1 : 0;
+  return a;
+}
+
+// <dA/dtheta x, y>: S_x = phase . N(F x), F y, then the weighted sums.
+template <typename T> isam_status param_grad_impl(isam_plan* P, const void* x, const void* y,
+                                                  double* grad) {
+  Impl<T>& im = impl_of<T>(P);
+  ISAM_TRY(calib_buffers<T>(P, im, 0));
+  cudaStream_t s = P->stream;
+  CUDA_TRY(cudaMemsetAsync(P->cpartial, 0, sizeof(double) * 5 * P->npairs, s));
+  ISAM_TRY(lat_forward<T>(P, im, x, im.eta_hat, P->nz, false));
+  ISAM_TRY(launch(P, ISAM_KCLASS_AX_FWD, [&] {
+    return launch_ax_fwd<T>(ax_args<T>(P, im, im.eta_hat, im.spec), P->npairs, s);
+  }));
+  ISAM_TRY(lat_forward<T>(P, im, y, im.spec2, P->nk, true));
+  ISAM_TRY(launch(P, ISAM_KCLASS_MISC, [&] {
+    return launch_param_reduce<T>(param_args<T>(P, im.spec, nullptr, im.spec2, T(1), false),
+                                  P->npairs, s);
+  }));
+  return read_param_partials(P, 1.0, grad);
+}
+
+isam_status check_unrolled_opts(const isam_plan* P, const isam_solve_opts* o, int every) {
+  if (!o || o->max_iter < 1 || every < 1) return ISAM_ERR_INVALID;
+  if (!(o->lambda_abs > 0) || !(o->L > 0) || !isfinite(o->lambda_abs) || !isfinite(o->L))
+    return ISAM_ERR_INVALID;
+  if (o->residual_addback) return ISAM_ERR_INVALID;
+  (void)P;
+  return ISAM_OK;
+}
+
+// z^K of K = o->max_iter iterations from z^0 = 0; before iteration c*every+1
+// the pair (z^{c every}, z^{c every - 1}) is copied to ckpt images 2c, 2c+1.
+template <typename T> isam_status unrolled_impl(isam_plan* P, const T* s_d,
+                                                const isam_solve_opts* o, int every,
+                                                cplx<T>* ckpt, cplx<T>* z_out) {
+  Impl<T>& im = impl_of<T>(P);
+  ISAM_TRY(calib_buffers<T>(P, im, 0));
+  cudaStream_t s = P->stream;
+  const size_t bytes = sizeof(cplx<T>) * P->n_img;
+  const int K = o->max_iter;
+  std::vector<double> mu;
+  momentum(K + 1, mu);
+  cplx<T>* zP = im.zA;
+  cplx<T>* zQ = im.zB;
+  CUDA_TRY(cudaMemsetAsync(P->flag, 0, sizeof(int), s));
+  CUDA_TRY(cudaMemsetAsync(zP, 0, bytes, s));
+  CUDA_TRY(cudaMemsetAsync(zQ, 0, bytes, s));
+  CUDA_TRY(cudaMemsetAsync(im.eta_hat, 0, bytes, s));
+  ISAM_TRY(lat_forward<T>(P, im, s_d, im.sdh, P->nk, true));
+  const T* w = static_cast<const T*>(o->w_dev);
+  for (int k = 1; k <= K; ++k) {
+    if ((k - 1) % every == 0 && ckpt) {
+      const size_t c = size_t((k - 1) / every);
+      CUDA_TRY(cudaMemcpyAsync(ckpt + 2 * c * P->n_img, zP, bytes, cudaMemcpyDeviceToDevice, s));
+      CUDA_TRY(cudaMemcpyAsync(ckpt + (2 * c + 1) * P->n_img, zQ, bytes, cudaMemcpyDeviceToDevice, s));
+    }
+    ISAM_TRY(fista_iteration<T>(P, im, zP, zQ, zQ, w, o->lambda_abs, o->L, mu[k - 1], mu[k], false));
+    std::swap(zP, zQ);
+  }
+  CUDA_TRY(cudaMemcpyAsync(z_out, zP, bytes, cudaMemcpyDeviceToDevice, s));
+  int flag = 0;
+  CUDA_TRY(cudaMemcpyAsync(&flag, P->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  harvest_events(P);
+  return flag ? ISAM_ERR_NONFINITE : ISAM_OK;
+}
+
+// Gradient of <z_bar, z^K> with respect to theta (and s_d when s_bar is
+// given).  Segment by segment from the last: recompute its iterations from
+// the checkpoint, keeping u^k and eta_hat^k, then run the reverse recursion
+//   ubar = J_T(u^k)^T zbar^k,  etabar = ubar - (1/L) A^H A ubar,
+//   theta_bar -= (1/L)(<dA ubar, A eta^k - s_d> + <A ubar, dA eta^k>),
+//   s_bar += (1/L) A ubar,  zbar^{k-1} += (1 + mu_{k-1}) etabar,
+//   zbar^{k-2} -= mu_{k-1} etabar.
+template <typename T> isam_status unrolled_vjp_impl(isam_plan* P, const T* s_d,
+                                                    const isam_solve_opts* o, int every,
+                                                    const cplx<T>* ckpt, const cplx<T>* z_bar,
+                                                    T* s_bar, double* grad) {
+  Impl<T>& im = impl_of<T>(P);
+  const int K = o->max_iter;
+  const int C = std::min(every, K);
+  ISAM_TRY(calib_buffers<T>(P, im, C));
+  cudaStream_t s = P->stream;
+  const size_t n = P->n_img, bytes = sizeof(cplx<T>) * n;
+  const double L = o->L, lam = o->lambda_abs;
+  const T* w = static_cast<const T*>(o->w_dev);
+  std::vector<double> mu;
+  momentum(K + 1, mu);
+  cplx<T>* seg_u = im.seg;              // [C] images u^k
+  cplx<T>* seg_eh = im.seg + C * n;     // [C + 1] images eta_hat^k
+  cplx<T>* zb[3] = {im.cal, im.cal + n, im.cal + 2 * n};
+  cplx<T>* ubar = im.cal + 3 * n;
+  cplx<T>* bimg = im.cal + 4 * n;
+  CUDA_TRY(cudaMemsetAsync(P->flag, 0, sizeof(int), s));
+  CUDA_TRY(cudaMemsetAsync(P->cpartial, 0, sizeof(double) * 5 * P->npairs, s));
+  CUDA_TRY(cudaMemcpyAsync(zb[0], z_bar, bytes, cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaMemsetAsync(zb[1], 0, 2 * bytes, s));
+  if (s_bar) CUDA_TRY(cudaMemsetAsync(s_bar, 0, sizeof(T) * P->n_spec, s));
+  ISAM_TRY(lat_forward<T>(P, im, s_d, im.sdh, P->nk, true));
+  int cur = 0;                          // zb[cur] = zbar^k, then zbar^{k-1}, zbar^{k-2}
+  const int nseg = (K + C - 1) / C;
+  for (int sg = nseg - 1; sg >= 0; --sg) {
+    const int k0 = sg * C, k1 = std::min(K, k0 + C);
+    // recompute iterations k0+1 .. k1 from (z^{k0}, z^{k0-1})
+    CUDA_TRY(cudaMemcpyAsync(im.zA, ckpt + 2 * size_t(sg) * n, bytes, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(im.zB, ckpt + (2 * size_t(sg) + 1) * n, bytes,
+                             cudaMemcpyDeviceToDevice, s));
+    ISAM_TRY(launch(P, ISAM_KCLASS_MISC, [&] {
+      return launch_extrapolate<T>(im.zA, im.zB, T(mu[k0]), im.grad, n, s);
+    }));
+    ISAM_TRY(lat_forward<T>(P, im, im.grad, seg_eh, P->nz, false));
+    cplx<T>* zP = im.zA;
+    cplx<T>* zQ = im.zB;
+    for (int k = k0 + 1; k <= k1; ++k) {
+      const int i = k - k0 - 1;
+      ISAM_TRY(fista_iteration<T>(P, im, zP, zQ, zQ, w, lam, L, mu[k - 1], mu[k], false,
+                                  seg_eh + i * n, seg_eh + (i + 1) * n, seg_u + i * n));
+      std::swap(zP, zQ);
+    }
+    // reverse through the segment
+    for (int k = k1; k > k0; --k) {
+      const int i = k - k0 - 1;
+      cplx<T>* zcur = zb[cur];
+      cplx<T>* zm1 = zb[(cur + 1) % 3];
+      cplx<T>* zm2 = zb[(cur + 2) % 3];
+      ISAM_TRY(launch(P, ISAM_KCLASS_MISC, [&] {
+        return launch_st_vjp<T>(seg_u + i * n, zcur, w, T(lam / L), P->nz, ubar, n, s);
+      }));
+      // S_ubar and S_eta (lateral spectra of K_hat before the real part)
+      ISAM_TRY(lat_forward<T>(P, im, ubar, im.eta_hat, P->nz, false));
+      ISAM_TRY(launch(P, ISAM_KCLASS_AX_FWD, [&] {
+        return launch_ax_fwd<T>(ax_args<T>(P, im, im.eta_hat, im.spec), P->npairs, s);
+      }));
+      ISAM_TRY(launch(P, ISAM_KCLASS_AX_FWD, [&] {
+        return launch_ax_fwd<T>(ax_args<T>(P, im, seg_eh + i * n, im.spec2), P->npairs, s);
+      }));
+      // theta partials; im.spec becomes F(A ubar)
+      ISAM_TRY(launch(P, ISAM_KCLASS_MISC, [&] {
+        return launch_param_reduce<T>(param_args<T>(P, im.spec, im.spec2, im.sdh, T(-1), true),
+                                      P->npairs, s);
+      }));
+      // b = A^H A ubar
+      ISAM_TRY(launch(P, ISAM_KCLASS_AX_ADJ, [&] {
+        return launch_ax_adj<T>(ax_args<T>(P, im, im.spec, im.grad), P->npairs, s);
+      }));
+      if (s_bar) {
+        ISAM_TRY(lat_inverse<T>(P, im, im.spec, im.s_tmp, P->nk, true));
+        ISAM_TRY(launch(P, ISAM_KCLASS_MISC, [&] {
+          return launch_caxpy<T>(reinterpret_cast<const cplx<T>*>(s_bar),
+                                 reinterpret_cast<const cplx<T>*>(im.s_tmp), T(1.0 / L),
+                                 reinterpret_cast<cplx<T>*>(s_bar), P->n_spec / 2, s);
+        }));
+      }
+      ISAM_TRY(lat_inverse<T>(P, im, im.grad, bimg, P->nz, false));
+      ISAM_TRY(launch(P, ISAM_KCLASS_MISC, [&] {
+        return launch_bwd_combine<T>(ubar, bimg, T(1.0 / L), T(mu[k - 1]), k - 1 >= 1 ? zm1 : nullptr,
+                                     k - 2 >= 1 ? zm2 : nullptr, n, s);
+      }));
+      CUDA_TRY(cudaMemsetAsync(zcur, 0, bytes, s));   // becomes zbar^{k-3}
+      cur = (cur + 1) % 3;
+    }
+  }
+  int flag = 0;
+  CUDA_TRY(cudaMemcpyAsync(&flag, P->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  ISAM_TRY(read_param_partials(P, -1.0 / L, grad));
+  return flag ? ISAM_ERR_NONFINITE : ISAM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+isam_status isam_set_model(isam_plan* P, int32_t n_disp, const double* disp, double z0) {
+  if (!P || n_disp < 0 || n_disp > 4 || (n_disp > 0 && !disp) || !isfinite(z0))
+    return ISAM_ERR_INVALID;
+  for (int i = 0; i < n_disp; ++i)
+    if (!isfinite(disp[i])) return ISAM_ERR_INVALID;
+  DeviceGuard g(P->device);
+  CUDA_TRY(cudaStreamSynchronize(P->stream));
+  P->p.n_disp = n_disp;
+  for (int i = 0; i < 4; ++i) P->p.disp[i] = i < n_disp ? disp[i] : 0.0;
+  P->p.z0 = z0;
+  make_stolt(P);
+  if (P->f32.ready) ISAM_TRY(phase_tables<float>(P, P->f32));
+  if (P->f64.ready) ISAM_TRY(phase_tables<double>(P, P->f64));
+  P->L_cache = 0.0;
+  return from_cuda(cudaStreamSynchronize(P->stream));
+}
+
+isam_status isam_param_grad(isam_plan* P, const void* x, const void* y, double* grad) {
+  if (!P || !x || !y || !grad) return ISAM_ERR_INVALID;
+  DeviceGuard g(P->device);
+  P->launches = 0;
+  if (P->p.precision == ISAM_FP64) return param_grad_impl<double>(P, x, y, grad);
+  return param_grad_impl<float>(P, x, y, grad);
+}
+
+int32_t isam_unrolled_checkpoint_images(int32_t K, int32_t every) {
+  if (K < 1 || every < 1) return -1;
+  return 2 * ((K + every - 1) / every);
+}
+
+isam_status isam_fista_unrolled(isam_plan* P, const void* s_d, const isam_solve_opts* o,
+                                int32_t every, void* ckpt, void* z_out) {
+  if (!P || !s_d || !z_out) return ISAM_ERR_INVALID;
+  ISAM_TRY(check_unrolled_opts(P, o, every));
+  DeviceGuard g(P->device);
+  P->launches = 0;
+  if (P->p.precision == ISAM_FP64)
+    return unrolled_impl<double>(P, static_cast<const double*>(s_d), o, every,
+                                 static_cast<double2*>(ckpt), static_cast<double2*>(z_out));
+  return unrolled_impl<float>(P, static_cast<const float*>(s_d), o, every,
+                              static_cast<float2*>(ckpt), static_cast<float2*>(z_out));
+}
+
+isam_status isam_fista_unrolled_vjp(isam_plan* P, const void* s_d, const isam_solve_opts* o,
+                                    int32_t every, const void* ckpt, const void* z_bar,
+                                    void* s_bar, double* grad) {
+  if (!P || !s_d || !ckpt || !z_bar || !grad) return ISAM_ERR_INVALID;
+  ISAM_TRY(check_unrolled_opts(P, o, every));
+  DeviceGuard g(P->device);
+  P->launches = 0;
+  if (P->p.precision == ISAM_FP64)
+    return unrolled_vjp_impl<double>(P, static_cast<const double*>(s_d), o, every,
+                                     static_cast<const double2*>(ckpt),
+                                     static_cast<const double2*>(z_bar),
+                                     static_cast<double*>(s_bar), grad);
+  return unrolled_vjp_impl<float>(P, static_cast<const float*>(s_d), o, every,
+                                  static_cast<const float2*>(ckpt),
+                                  static_cast<const float2*>(z_bar), static_cast<float*>(s_bar),
+                                  grad);
 }
 
 }  // extern "C"

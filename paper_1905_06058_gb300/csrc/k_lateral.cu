@@ -150,9 +150,11 @@ __global__ void __launch_bounds__(512, 2) k_lat(const __grid_constant__ LatArgs<
       const V eta = eadd(z1, escale(esub(z1, z2v[i]), a.mu_prev));
       const T tau0 = a.w ? a.lam_over_L * a.w[n0] : a.lam_over_L;
       const T tau1 = a.w ? a.lam_over_L * a.w[n0 + 1] : a.lam_over_L;
+      const V u = esub(eta, g);
+      if (a.uout) *reinterpret_cast<V*>(a.uout + gi) = u;
       V z;
-      z.a = soft_threshold(csub(eta.a, g.a), tau0);
-      z.b = soft_threshold(csub(eta.b, g.b), tau1);
+      z.a = soft_threshold(u.a, tau0);
+      z.b = soft_threshold(u.b, tau1);
       *reinterpret_cast<V*>(a.zout + gi) = z;
       buf[sidx(e)] = eadd(z, escale(esub(z, z1), a.mu));
       if (a.partial) {

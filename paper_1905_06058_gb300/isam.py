@@ -75,7 +75,18 @@ _SIGS = {
     "isam_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]),
     "isam_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "isam_set_model": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.c_double]),
+    "isam_param_grad": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
+    "isam_unrolled_checkpoint_images": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_int32]),
+    "isam_fista_unrolled": (ctypes.c_int, [_P, _P, ctypes.POINTER(SolveOpts), ctypes.c_int32,
+                                           _P, _P]),
+    "isam_fista_unrolled_vjp": (ctypes.c_int, [_P, _P, ctypes.POINTER(SolveOpts),
+                                               ctypes.c_int32, _P, _P, _P,
+                                               ctypes.POINTER(ctypes.c_double)]),
 }
+N_PARAMS = 5
+PARAM_NAMES = ("a1", "a2", "a3", "a4", "z0")
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
     _f.restype = _res
@@ -258,6 +269,67 @@ class Plan:
         _check(_lib.isam_lipschitz(self._h, int(iters), float(rtol), p, ctypes.byref(L)),
                "isam_lipschitz")
         return L.value
+
+    # -- calibration of theta = (a1, a2, a3, a4, z0) -----------------------------
+    def set_model(self, disp, z0: float) -> None:
+        """isam_set_model: new dispersion coefficients a_1.. (up to 4) and focal depth."""
+        self._sync_stream()
+        self._theta = None
+        d = [float(v) for v in disp]
+        arr = (ctypes.c_double * 4)(*(d + [0.0] * (4 - len(d))))
+        _check(_lib.isam_set_model(self._h, len(d), arr, float(z0)), "isam_set_model")
+
+    def param_grad(self, x, y):
+        """isam_param_grad: <dA/dtheta x, y> for theta = (a1..a4, z0), as a float64 array."""
+        import numpy as np
+        self._sync_stream()
+        g = (ctypes.c_double * N_PARAMS)()
+        _check(_lib.isam_param_grad(self._h, self._dev(x, self.cplx_dtype, self.image_shape, "x"),
+                                    self._dev(y, self.real_dtype, self.spec_shape, "y"), g),
+               "isam_param_grad")
+        return np.array(g[:], dtype=np.float64)
+
+    def _unrolled_opts(self, lam, L, K, w):
+        return self._opts(0.0, lam, K, 0.0, 1, w, False, L, 0.0)
+
+    def fista_unrolled(self, s, lam: float, L: float, K: int, every: int = 5, w=None,
+                       checkpoints: bool = True):
+        """isam_fista_unrolled: (z^K, checkpoint images or None)."""
+        import torch
+        self._sync_stream()
+        o = self._unrolled_opts(lam, L, K, w)
+        z = torch.empty(self.image_shape, dtype=self.cplx_dtype, device=s.device)
+        ck = None
+        if checkpoints:
+            n = int(_lib.isam_unrolled_checkpoint_images(int(K), int(every)))
+            ck = torch.empty((n,) + self.image_shape, dtype=self.cplx_dtype, device=s.device)
+        _check(_lib.isam_fista_unrolled(self._h, self._dev(s, self.real_dtype, self.spec_shape, "s"),
+                                        ctypes.byref(o), int(every),
+                                        None if ck is None else _P(ck.data_ptr()),
+                                        self._dev(z, self.cplx_dtype, self.image_shape, "z")),
+               "isam_fista_unrolled")
+        return z, ck
+
+    def fista_unrolled_vjp(self, s, lam: float, L: float, K: int, every: int, ckpt, z_bar,
+                           want_s_bar: bool = False, w=None):
+        """isam_fista_unrolled_vjp: (d<z_bar, z^K>/dtheta as float64 array, d/ds_d or None)."""
+        import numpy as np
+        import torch
+        self._sync_stream()
+        o = self._unrolled_opts(lam, L, K, w)
+        n = int(_lib.isam_unrolled_checkpoint_images(int(K), int(every)))
+        if ckpt is None or tuple(ckpt.shape) != (n,) + self.image_shape or \
+                ckpt.dtype != self.cplx_dtype or not ckpt.is_cuda or not ckpt.is_contiguous():
+            raise ValueError(f"ckpt: need contiguous CUDA {self.cplx_dtype} {(n,) + self.image_shape}")
+        sb = torch.empty(self.spec_shape, dtype=self.real_dtype, device=s.device) \
+            if want_s_bar else None
+        g = (ctypes.c_double * N_PARAMS)()
+        _check(_lib.isam_fista_unrolled_vjp(
+            self._h, self._dev(s, self.real_dtype, self.spec_shape, "s"), ctypes.byref(o),
+            int(every), _P(ckpt.data_ptr()),
+            self._dev(z_bar, self.cplx_dtype, self.image_shape, "z_bar"),
+            None if sb is None else _P(sb.data_ptr()), g), "isam_fista_unrolled_vjp")
+        return np.array(g[:], dtype=np.float64), sb
 
     def max_abs(self, eta) -> float:
         self._sync_stream()
