@@ -20,6 +20,8 @@ What it computes (paper section / equation in brackets):
 * weighted complex soft threshold [Eq. 14], relative residual [Eq. 15],
   FISTA [Alg. 1], residual add-back [Alg. 1, optional last step];
 * Lipschitz constant of the gradient by power iteration;
+* the 1-D per-A-scan model of the DEFR objective (Eq. 10) and the
+  dispersion-compensated IFFT (Eq. 9);
 * derivatives for calibrating the dispersion coefficients a_1..a_4 (Eq. 7)
   and the focal depth z0 by gradient descent: <dA/dtheta x, y>, the
   Jacobian-transpose of the soft threshold (Eq. 14), and the gradient of
@@ -460,6 +462,35 @@ def dense_real_matrix(op: IsamOracle) -> np.ndarray:
         e[i] = 1j
         M[:, n + i] = op.forward(e.reshape(op.image_shape)).ravel()
     return M
+
+
+class AxialModelOracle:
+    """The 1-D dispersion-encoded model of each A-scan on its own (the model of
+    the DEFR objective, Eq. 10, with our scaling): every lateral position is an
+    independent nx = ny = 1 problem, s(x, k) = Re(e^{j phi(k)} N(eta(x, .))(k)),
+    no lateral coupling and no focus term (2k + beta = 0 at q = 0)."""
+
+    def __init__(self, g, mode: str = "nufft", J: int = 6):
+        import dataclasses
+        self.g = g
+        self.col = IsamOracle(dataclasses.replace(g, nx=1, ny=1, dy=0.0), mode, J)
+        nz = g.nz or g.nk
+        self.image_shape = (g.ny, g.nx, nz)
+        self.spec_shape = (g.ny, g.nx, g.nk)
+
+    def forward(self, eta: np.ndarray) -> np.ndarray:
+        out = np.zeros(self.spec_shape)
+        for iy in range(self.g.ny):
+            for ix in range(self.g.nx):
+                out[iy, ix] = self.col.forward(eta[iy, ix][None, None, :])[0, 0]
+        return out
+
+    def adjoint(self, y: np.ndarray) -> np.ndarray:
+        out = np.zeros(self.image_shape, np.complex128)
+        for iy in range(self.g.ny):
+            for ix in range(self.g.nx):
+                out[iy, ix] = self.col.adjoint(y[iy, ix][None, None, :])[0, 0]
+        return out
 
 
 def dispersion_compensated_ifft(g, s_d: np.ndarray) -> np.ndarray:
