@@ -44,6 +44,8 @@ def parse_args():
     ap.add_argument("--no-extras", action="store_true", help="skip A+A^H, FP64 and volume lines")
     ap.add_argument("--volume", action="store_true", help="also time the 256^2 x 2048 volume")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--calib-steps", type=int, default=10,
+                    help="Adam steps timed in the calibration line")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--L", type=float, default=0.0,
                     help="Lipschitz constant to use (0: power-iteration estimate, cached)")
@@ -365,6 +367,7 @@ def run_extras(torch, plan, s_d, wl, args, L):
     ex["fp64_iters_per_s"] = it64 / (a.elapsed_time(b) / 1000.0)
     p64.close()
     ex["cufft_comparison_us"] = cufft_comparison(torch, plan)
+    ex["calibration"] = run_calibration(torch, args.calib_steps)
     if args.volume:
         ex["volume"] = run_volume(torch)
     return ex
@@ -394,6 +397,41 @@ def cufft_comparison(torch, plan):
         out[name] = a.elapsed_time(b) / reps * 1000.0
     out["per_iteration_4_ffts"] = 2 * out["lateral_fft_nx"] + 2 * out["axial_fft_2nz_zero_padded"]
     return out
+
+
+def run_calibration(torch, steps: int):
+    """Calibration of (a2, a3, z0): Adam steps on the data fidelity of 16 B-scans
+    (512 x 2048) through K = 20 unrolled FISTA iterations with checkpoints every
+    5; one step is the unrolled solves, the model, and the gradient of all
+    B-scans.  The spectra are made by the plan's own model at the hidden theta
+    plus Gaussian noise; lambda and L are fixed at the start theta."""
+    from paper_1905_06058_gb300 import calib
+    from paper_1905_06058_gb300 import inputs as I
+    from paper_1905_06058_gb300.isam import Plan
+    wl = I.config5()
+    plan = Plan(wl.geom)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(wl.K)
+    spectra = []
+    for eta in wl.etas:
+        s = plan.forward(torch.from_numpy(eta).cuda())
+        sigma = float(torch.linalg.vector_norm(s)) / (s.numel() ** 0.5 * 10 ** (wl.snr_db / 20))
+        spectra.append(s + sigma * torch.randn(s.shape, generator=gen, device="cuda"))
+    plan.set_model(wl.start[:4].tolist(), float(wl.start[4]))
+    L = plan.lipschitz(iters=100, rtol=1e-6)
+    lams = [wl.lambda_rel * plan.max_abs(plan.adjoint(s)) for s in spectra]
+    calib.calibrate(plan, spectra, wl.start, lams, L, wl.K, wl.every, steps=1)   # warm-up
+    res = calib.calibrate(plan, spectra, wl.start, lams, L, wl.K, wl.every, steps=steps)
+    scale = calib.theta_scales(wl.geom)
+    truth = np.array(list(wl.geom.disp) + [wl.geom.z0])
+    err = lambda th: [float(abs(th[i] - truth[i]) / scale[i]) for i in (1, 2, 4)]
+    plan.close()
+    return {"workload": wl.name, "K": wl.K, "checkpoint_every": wl.every, "steps": steps,
+            "adam_steps_per_s": steps / res.seconds,
+            "ms_per_bscan_step": res.seconds / steps / len(spectra) * 1e3,
+            "loss_first": res.losses[0], "loss_last": res.losses[-1],
+            "theta_error_start_a2_a3_z0": err(wl.start), "theta_error_end_a2_a3_z0": err(res.theta),
+            "units": "a_i: rad at the band edge; z0: fraction of the depth range"}
 
 
 def run_volume(torch):

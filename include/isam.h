@@ -79,6 +79,12 @@ typedef struct {
  * plan tabulates them when the table takes at most 64 MiB (B-scans) and the
  * kernels evaluate them otherwise (volumes).  This flag forces evaluation. */
 #define ISAM_FLAG_NO_STOLT_TABLE 1
+/* The 1-D dispersion-encoded model of each A-scan on its own, the model of the
+ * DEFR objective (Eq. 10, our scaling): every column uses the q = 0 Stolt map
+ * (beta = -2k), so there is no lateral coupling and no focus term; dx, dy, na
+ * and z0 have no effect.  Forward, adjoint, solve and calibration calls then
+ * work on this model (MBIR on Eq. 10 with the weighted l1 prior). */
+#define ISAM_FLAG_AXIAL_MODEL 4
 
 typedef struct isam_plan isam_plan;
 
@@ -164,6 +170,13 @@ isam_status isam_max_abs(isam_plan* plan, const void* eta, double* out);
 #define ISAM_NOALLOC_MAX_PARTIALS 65536
 isam_status isam_max_abs_noalloc(const void* x, int64_t n, int32_t precision, double* out,
                                  void* stream);
+
+/* The direct dispersion-compensated reconstruction of Eq. 9 on the full-range
+ * depth grid, A-scan by A-scan (the exact adjoint of the ISAM_FLAG_AXIAL_MODEL
+ * operator, evaluated as an nz-point FFT):
+ *   eta(x, n) = (1/sqrt(nz)) sum_j s_d(x, k_j) e^{-j phi(k_j)} e^{-j 2 k_j z_n}.
+ * s_d: device spectra, eta: device image.  Asynchronous on the plan's stream. */
+isam_status isam_dispersion_compensated_ifft(isam_plan* plan, const void* s_d, void* eta);
 
 /* ---- Calibration of the dispersion coefficients and the focal depth -------
  * The paper notes that a (Eq. 7) may be found by an autofocus method (§2)

@@ -151,6 +151,11 @@ template <typename T> cudaError_t launch_bwd_combine(const cplx<T>* ubar, const 
                                                      T inv_L, T mu, cplx<T>* zb1, cplx<T>* zb2,
                                                      size_t n, cudaStream_t s);
 
+// Eq. 9 direct reconstruction (k_direct.cu)
+template <typename T> cudaError_t launch_dc_ifft(const T* s, cplx<T>* out, const cplx<T>* disp,
+                                                 const cplx<T>* post, int nk, int nz, int lognz,
+                                                 int n_ascans, cudaStream_t st);
+
 int lat_tile(int L, int M);   // pair-columns per block of a lateral pass
 template <typename T> size_t lat_smem_bytes(int L, int TP);
 

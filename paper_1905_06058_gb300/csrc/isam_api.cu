@@ -40,6 +40,7 @@ template <typename T> struct Impl {
   cplx<T>* seg = nullptr;
   int seg_cap = 0;
   cplx<T>* cal = nullptr;       // [5][n_img]: zbar x 3, ubar, b
+  cplx<T>* dc_post = nullptr;   // [nz] output phase of the Eq. 9 reconstruction
   bool ready = false;
 };
 
@@ -158,7 +159,7 @@ template <typename T> void impl_free(Impl<T>& im) {
   cudaFree(im.eta_hat); cudaFree(im.spec); cudaFree(im.grad); cudaFree(im.sdh);
   cudaFree(im.zA); cudaFree(im.zB); cudaFree(im.s_tmp);
   cudaFree(im.s_host_stage); cudaFree(im.out_stage);
-  cudaFree(im.spec2); cudaFree(im.seg); cudaFree(im.cal);
+  cudaFree(im.spec2); cudaFree(im.seg); cudaFree(im.cal); cudaFree(im.dc_post);
   im = Impl<T>();
 }
 
@@ -539,7 +540,7 @@ isam_status validate(const isam_params* p) {
   const int os = p->nufft_os ? p->nufft_os : 2;
   if (os != 2) return ISAM_ERR_UNSUPPORTED;
   if (!isfinite(p->z0)) return ISAM_ERR_INVALID;
-  if (p->flags & ~ISAM_FLAG_NO_STOLT_TABLE) return ISAM_ERR_INVALID;
+  if (p->flags & ~(ISAM_FLAG_NO_STOLT_TABLE | ISAM_FLAG_AXIAL_MODEL)) return ISAM_ERR_INVALID;
   for (int i = 0; i < 4; ++i)
     if (!isfinite(p->disp[i])) return ISAM_ERR_INVALID;
   return ISAM_OK;
@@ -555,9 +556,11 @@ void make_stolt(isam_plan* P) {
   StoltConst& c = P->sc;
   const double dk = (p.k_max - p.k_min) / (P->nk - 1);
   c.kap = p.k_min / dk;
-  c.Qx = P->nx > 1 ? pow(2.0 * M_PI / (P->nx * p.dx * dk), 2.0) : 0.0;
-  c.Qy = P->ny > 1 ? pow(2.0 * M_PI / (P->ny * p.dy * dk), 2.0) : 0.0;
-  c.zeta = dk * p.z0 / (2.0 * M_PI);
+  // the 1-D model puts every column on the q = 0 map (no lateral coupling)
+  const bool axial = (p.flags & ISAM_FLAG_AXIAL_MODEL) != 0;
+  c.Qx = P->nx > 1 && !axial ? pow(2.0 * M_PI / (P->nx * p.dx * dk), 2.0) : 0.0;
+  c.Qy = P->ny > 1 && !axial ? pow(2.0 * M_PI / (P->ny * p.dy * dk), 2.0) : 0.0;
+  c.zeta = axial ? 0.0 : dk * p.z0 / (2.0 * M_PI);
   c.c0d = fmod(2.0 * c.kap, double(P->K));
   c.I0 = int(floor(c.c0d));
   c.f0 = float(c.c0d - double(c.I0));
@@ -568,7 +571,7 @@ void make_stolt(isam_plan* P) {
   split_ff(c.zeta, &c.zeta_hi, &c.zeta_lo);
   c.K = P->K; c.logK = ilog2(P->K);
   c.nx = P->nx; c.ny = P->ny; c.nk = P->nk; c.nz = P->nz; c.J = P->J;
-  c.focus = p.z0 != 0.0;
+  c.focus = c.zeta != 0.0;
 }
 
 // Least squares min ||V a - v|| for the Vandermonde V_ik = y_i^k (k <= deg),
@@ -1167,3 +1170,47 @@ isam_status isam_fista_unrolled_vjp(isam_plan* P, const void* s_d, const isam_so
 }
 
 }  // extern "C"
+
+namespace {
+
+template <typename T> isam_status dc_ifft_impl(isam_plan* P, const T* s, cplx<T>* out) {
+  Impl<T>& im = impl_of<T>(P);
+  if (!im.dc_post) {
+    // post_n = e^{-2 pi i kappa_0 (n - nz/2) / nz} / sqrt(nz), the phase reduced in FP64
+    std::vector<cplx<T>> h(P->nz);
+    const double dk = (P->p.k_max - P->p.k_min) / (P->nk - 1);
+    const double kap0 = P->p.k_min / dk;
+    const double kf = kap0 - floor(kap0);
+    const double kint = floor(kap0);
+    for (int n = 0; n < P->nz; ++n) {
+      const int m = n - P->nz / 2;
+      // kappa_0 m / nz = (kint m mod nz)/nz + kf m / nz, both reduced to turns
+      const double t1 = fmod(fmod(kint, double(P->nz)) * m, double(P->nz)) / P->nz;
+      const double turn = t1 + kf * m / P->nz;
+      const double ang = -2.0 * M_PI * (turn - floor(turn));
+      h[n] = mk<T>(T(cos(ang) / sqrt(double(P->nz))), T(sin(ang) / sqrt(double(P->nz))));
+    }
+    ISAM_TRY(dalloc(&im.dc_post, P->nz));
+    CUDA_TRY(cudaMemcpy(im.dc_post, h.data(), sizeof(cplx<T>) * P->nz, cudaMemcpyHostToDevice));
+  }
+  return launch(P, ISAM_KCLASS_MISC, [&] {
+    return launch_dc_ifft<T>(s, out, im.tab.disp, im.dc_post, P->nk, P->nz, ilog2(P->nz),
+                             P->nx * P->ny, P->stream);
+  });
+}
+
+}  // namespace
+
+extern "C" {
+
+isam_status isam_dispersion_compensated_ifft(isam_plan* P, const void* s_d, void* eta) {
+  if (!P || !s_d || !eta) return ISAM_ERR_INVALID;
+  DeviceGuard g(P->device);
+  P->launches = 0;
+  if (P->p.precision == ISAM_FP64)
+    return dc_ifft_impl<double>(P, static_cast<const double*>(s_d), static_cast<double2*>(eta));
+  return dc_ifft_impl<float>(P, static_cast<const float*>(s_d), static_cast<float2*>(eta));
+}
+
+}  // extern "C"
+

@@ -252,6 +252,37 @@ def config3(dtype=np.complex64, nx=256, nk=2048, n_points=5000) -> Workload:
     return Workload(f"volume_{nx}x{nx}x{nk}_fp32", g, eta, seed, 25.0, 0.02, 150)
 
 
+@dataclasses.dataclass
+class CalibWorkload:
+    """B-scans of one geometry made with a hidden dispersion and focal depth."""
+
+    name: str
+    geom: Geometry           # the hidden truth: geom.disp, geom.z0
+    etas: list               # specimens, [1, nx, nz] each
+    start: np.ndarray        # theta = (a1..a4, z0) where the fit starts
+    snr_db: float
+    lambda_rel: float
+    K: int
+    every: int
+
+
+def config5(n_bscans: int = 16, nx: int = 512, nk: int = 2048) -> CalibWorkload:
+    """16 B-scans of 512 x 2048 with hidden (a2, a3, z0); the fit starts with
+    a2 off by 0.6 rad and a3 by -0.4 rad at the band edge and z0 off by 1% of
+    the depth range.  K = 20 unrolled iterations, checkpoints every 5."""
+    seed = SEED_BASE + 5
+    rng = np.random.default_rng(seed)
+    g = _geometry(nx, 1, nk, nk, 0.1, 0.3, rng)
+    etas = [layered_specimen(np.random.default_rng(seed + 10 + b), (1, nx, nk), 3, 0.01, 100,
+                             np.complex64) for b in range(n_bscans)]
+    half = 0.5 * (g.k_max - g.k_min)
+    start = np.array(list(g.disp) + [g.z0], dtype=np.float64)
+    start[1] += 0.6 / half ** 2
+    start[2] -= 0.4 / half ** 3
+    start[4] += 0.01 * depth_range(g.k_min, g.k_max, nk)
+    return CalibWorkload(f"calib_{n_bscans}x{nx}x{nk}", g, etas, start, 30.0, 0.01, 20, 5)
+
+
 def small_bscan(nx=32, nk=64, nz=0, na=0.1, focus_frac=0.3, n_points=6, seed=7,
                 dispersion=True, dx_scale=1.0, min_sep=0, ny=1) -> Workload:
     """Small seeded case for parity tests (several tiles and a ragged tail)."""

@@ -23,6 +23,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 ISAM_FP32, ISAM_FP64 = 0, 1
 ISAM_FLAG_NO_STOLT_TABLE = 1
+ISAM_FLAG_AXIAL_MODEL = 4
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "CUDA error",
           4: "non-finite value in the solve", 5: "device wait timed out",
           6: "unsupported size or option"}
@@ -75,6 +76,7 @@ _SIGS = {
     "isam_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]),
     "isam_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "isam_dispersion_compensated_ifft": (ctypes.c_int, [_P, _P, _P]),
     "isam_set_model": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                       ctypes.c_double]),
     "isam_param_grad": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
@@ -108,7 +110,8 @@ def lib() -> ctypes.CDLL:
     return _lib
 
 
-def make_params(geom, precision: str = "fp32", J: int = 6, stolt_table: bool = True) -> IsamParams:
+def make_params(geom, precision: str = "fp32", J: int = 6, stolt_table: bool = True,
+                axial_model: bool = False) -> IsamParams:
     p = IsamParams()
     p.nx, p.ny, p.nk, p.nz = int(geom.nx), int(geom.ny), int(geom.nk), int(geom.nz or geom.nk)
     p.k_min, p.k_max = float(geom.k_min), float(geom.k_max)
@@ -121,7 +124,8 @@ def make_params(geom, precision: str = "fp32", J: int = 6, stolt_table: bool = T
     p.precision = ISAM_FP64 if precision == "fp64" else ISAM_FP32
     p.nufft_J = int(J)
     p.nufft_os = 2
-    p.flags = 0 if stolt_table else ISAM_FLAG_NO_STOLT_TABLE
+    p.flags = (0 if stolt_table else ISAM_FLAG_NO_STOLT_TABLE) | \
+        (ISAM_FLAG_AXIAL_MODEL if axial_model else 0)
     return p
 
 
@@ -135,7 +139,7 @@ class Plan:
     """A plan for one geometry: isam_plan_create / isam_forward / isam_adjoint / isam_solve."""
 
     def __init__(self, geom, precision: str = "fp32", J: int = 6, stream=None,
-                 stolt_table: bool = True):
+                 stolt_table: bool = True, axial_model: bool = False):
         import torch
         self.geom = geom
         self.precision = precision
@@ -143,7 +147,7 @@ class Plan:
         self.cplx_dtype = torch.complex128 if precision == "fp64" else torch.complex64
         self.image_shape = (geom.ny, geom.nx, geom.nz or geom.nk)
         self.spec_shape = (geom.ny, geom.nx, geom.nk)
-        self._params = make_params(geom, precision, J, stolt_table)
+        self._params = make_params(geom, precision, J, stolt_table, axial_model)
         h = _P()
         _check(_lib.isam_plan_create(ctypes.byref(self._params), _P(_stream_handle(stream)),
                                      ctypes.byref(h)), "isam_plan_create")
@@ -204,6 +208,18 @@ class Plan:
         _check(_lib.isam_adjoint(self._h, self._dev(s, self.real_dtype, self.spec_shape, "s"),
                                  self._dev(out, self.cplx_dtype, self.image_shape, "out")),
                "isam_adjoint")
+        return out
+
+    def dispersion_compensated_ifft(self, s, out=None):
+        """Eq. 9: the direct full-range reconstruction of every A-scan."""
+        import torch
+        self._sync_stream()
+        if out is None:
+            out = torch.empty(self.image_shape, dtype=self.cplx_dtype, device=s.device)
+        _check(_lib.isam_dispersion_compensated_ifft(
+            self._h, self._dev(s, self.real_dtype, self.spec_shape, "s"),
+            self._dev(out, self.cplx_dtype, self.image_shape, "out")),
+            "isam_dispersion_compensated_ifft")
         return out
 
     def _opts(self, lambda_rel, lambda_abs, max_iter, tol, check_every, w, addback, L, eps):
