@@ -60,7 +60,7 @@ enum { ISAM_FP32 = 0, ISAM_FP64 = 1 };
 /* Acquisition geometry and numerics: the problem as the paper states it
  * (spectral samples, lateral grid, NA and focus, dispersion; §2, §4.1). */
 typedef struct {
-  int32_t nx, ny;      /* lateral samples (powers of two, 1..4096); ny = 1: B-scan */
+  int32_t nx, ny;      /* lateral samples, 2^p or 3*2^p (p >= 3), <= 4096; ny = 1: B-scan */
   int32_t nk;          /* spectral samples per A-scan (power of two, 16..4096)      */
   int32_t nz;          /* depth samples of the image (power of two, >= 16); 0: nk   */
   double k_min, k_max; /* band edges, rad/m (k_max > k_min > 0)                     */

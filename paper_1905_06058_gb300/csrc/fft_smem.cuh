@@ -1,6 +1,8 @@
-// Shared-memory Stockham FFTs of power-of-two length, radix 8 with one
-// radix-4 or radix-2 tail pass.  Every participating thread owns eight points
-// per pass, so a length-L transform of one column takes L/8 threads.  Many
+// Shared-memory Stockham FFTs of length L = 2^p or 3 * 2^p (p >= 3): radix-8
+// passes, one radix-4 or radix-2 pass for the rest of 2^p, and for L = 3 * 2^p
+// a final radix-3 pass.  Every participating thread owns eight points per
+// power-of-two pass, so a length-L transform of one column takes L/8 threads
+// (each takes two or three of the L/3 radix-3 butterflies).  Many
 // columns can be transformed together: element r of column c lives at
 // buf[r * stride + c]; the caller maps threads to (column, butterfly).
 //
@@ -118,7 +120,7 @@ __device__ __forceinline__ void sincospi_(double x, double* s, double* c) { sinc
 // w_k = e^{-2 pi i k / (Ns R)}, k < Ns.  A butterfly raises w_k to the powers
 // r = 2 .. R-1 itself by repeated complex multiplication, so each pass reads
 // one table entry per butterfly instead of R - 1.
-__host__ __device__ __forceinline__ int twiddle_entries(int L, int logL) {
+__host__ __device__ __forceinline__ int twiddle_entries(int L, int logL, int r3 = 0) {
   if (L < 8) return 0;
   int n = 0, Ns = 1;
   const int n8 = logL / 3;
@@ -128,18 +130,21 @@ __host__ __device__ __forceinline__ int twiddle_entries(int L, int logL) {
   }
   const int rem = logL - 3 * n8;
   if (rem && Ns > 1) n += Ns;
+  if (rem) Ns <<= rem;
+  if (r3) n += Ns;
   return n;
 }
 
-// All threads of the block fill the table (ends with a barrier).
+// All threads of the block fill the table (ends with a barrier).  logL is
+// log2 of the power-of-two factor; r3 = 1 for L = 3 * 2^logL.
 template <typename T>
-__device__ __forceinline__ void build_twiddles(cplx<T>* tab, int L, int logL) {
+__device__ __forceinline__ void build_twiddles(cplx<T>* tab, int L, int logL, int r3 = 0) {
   if (L >= 8) {
     const int n8 = logL / 3, rem = logL - 3 * n8;
-    const int npass = n8 + (rem ? 1 : 0);
+    const int npass = n8 + (rem ? 1 : 0) + r3;
     int off = 0, Ns = 1;
     for (int p = 0; p < npass; ++p) {
-      const int R = p < n8 ? 8 : (rem == 2 ? 4 : 2);
+      const int R = p < n8 ? 8 : (p == n8 && rem ? (rem == 2 ? 4 : 2) : 3);
       if (Ns > 1) {
         for (int k = threadIdx.x; k < Ns; k += blockDim.x) {
           T s, c;
@@ -209,14 +214,55 @@ __device__ __forceinline__ void stockham_pass(E* buf, int stride, int col, int b
   __syncthreads();
 }
 
-// Length-L transform (L = 2^logL, 1 <= L <= 8192) of column `col`, using the
-// twiddle table built by build_twiddles.  For L >= 8 the active threads own
-// butterfly b < L/8; for L < 8 the thread with b == 0 transforms the column
-// directly.  HALF_ZERO: rows [L/4, 3L/4) of the input are zero (and need not
-// be stored).  Every thread of the block must call it; it ends with a barrier.
+// Final radix-3 pass of an L = 3 Ns transform (Ns = 2^p, the span reached by
+// the power-of-two passes): butterfly j < Ns reads rows j, j + Ns, j + 2 Ns,
+// multiplies by w^r (w = e^{SIGN 2 pi i j / (3 Ns)}), takes the 3-point DFT
+// and writes rows j, j + Ns, j + 2 Ns.  Thread b takes j = b + u L/8, u < 3.
+// Reads all its inputs, block barrier, writes.  Every thread must reach it.
+template <int SIGN, typename T, typename E>
+__device__ __forceinline__ void stockham_pass3(E* buf, int stride, int col, int b, int L, int Ns,
+                                               const cplx<T>* tw, bool active) {
+  const int L8 = L >> 3;
+  E v[9];
+#pragma unroll
+  for (int u = 0; u < 3; ++u) {
+    const int j = b + u * L8;
+    if (active && j < Ns) {
+#pragma unroll
+      for (int r = 0; r < 3; ++r) v[3 * u + r] = buf[prow(j + r * Ns) * stride + col];
+    }
+  }
+  __syncthreads();
+  const T h = T(0.86602540378443864676);   // sqrt(3)/2
+#pragma unroll
+  for (int u = 0; u < 3; ++u) {
+    const int j = b + u * L8;
+    if (active && j < Ns) {
+      cplx<T> w1 = tw[j];
+      if (SIGN > 0) w1.y = -w1.y;
+      E* a = v + 3 * u;
+      a[1] = emul(a[1], w1);
+      a[2] = emul(a[2], cmul(w1, w1));
+      const E t1 = eadd(a[1], a[2]);
+      const E t2 = esub(a[0], escale(t1, T(0.5)));
+      const E t3 = escale(emul_i<SIGN>(esub(a[1], a[2])), h);
+      buf[prow(j) * stride + col] = eadd(a[0], t1);
+      buf[prow(j + Ns) * stride + col] = eadd(t2, t3);
+      buf[prow(j + 2 * Ns) * stride + col] = esub(t2, t3);
+    }
+  }
+  __syncthreads();
+}
+
+// Length-L transform (L = 2^logL, or 3 * 2^logL when r3, L <= 8192) of column
+// `col`, using the twiddle table built by build_twiddles.  For L >= 8 the
+// active threads own butterfly b < L/8; for L < 8 the thread with b == 0
+// transforms the column directly.  HALF_ZERO: rows [L/4, 3L/4) of the input
+// are zero (and need not be stored; powers of two only).  Every thread of the
+// block must call it; it ends with a barrier.
 template <int SIGN, bool HALF_ZERO, typename T, typename E>
 __device__ __forceinline__ void fft_smem(E* buf, int stride, int col, int b, int L, int logL,
-                                         const cplx<T>* tw, bool active) {
+                                         const cplx<T>* tw, bool active, int r3 = 0) {
   if (L >= 8) {
     int Ns = 1;
     const int n8 = logL / 3;
@@ -231,6 +277,11 @@ __device__ __forceinline__ void fft_smem(E* buf, int stride, int col, int b, int
     const int rem = logL - 3 * n8;
     if (rem == 2) stockham_pass<SIGN, 4, false, T>(buf, stride, col, b, L, Ns, tw, active);
     else if (rem == 1) stockham_pass<SIGN, 2, false, T>(buf, stride, col, b, L, Ns, tw, active);
+    if (rem) {
+      if (Ns > 1) tw += Ns;
+      Ns <<= rem;
+    }
+    if (r3) stockham_pass3<SIGN, T>(buf, stride, col, b, L, Ns, tw, active);
   } else {
     __syncthreads();
     if (active && b == 0 && L > 1) {

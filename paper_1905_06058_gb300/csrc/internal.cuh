@@ -67,6 +67,7 @@ template <typename T> struct LatArgs {
   const void* in;        // complex (or real for R2C)
   void* out;             // complex (or real for INV_REAL)
   int B, L, logL, M;     // data viewed as [B][L][M], transform along L
+  int r3;                // L = 3 * 2^logL (else L = 2^logL)
   int TZ, logTZ;         // pair-columns (2 columns each) per block
   T norm;                // 1/sqrt(L)
   // LAT_UPDATE
@@ -158,5 +159,7 @@ template <typename T> cudaError_t launch_dc_ifft(const T* s, cplx<T>* out, const
 
 int lat_tile(int L, int M);   // pair-columns per block of a lateral pass
 template <typename T> size_t lat_smem_bytes(int L, int TP);
+// L = 2^log2 or 3 * 2^log2 (log2 >= 3): *log2, *r3; false for other lengths
+bool fft_length(int L, int* log2, int* r3);
 
 }  // namespace isam

@@ -240,7 +240,8 @@ template <typename T>
 LatArgs<T> lat_args(int B, int L, int M, const void* in, void* out) {
   LatArgs<T> a{};
   a.in = in; a.out = out;
-  a.B = B; a.L = L; a.logL = ilog2(L); a.M = M;
+  a.B = B; a.L = L; a.M = M;
+  fft_length(L, &a.logL, &a.r3);
   a.TZ = lat_tile(L, M); a.logTZ = ilog2(a.TZ);
   a.norm = T(1.0 / sqrt(double(L)));
   return a;
@@ -526,7 +527,9 @@ template <typename T> isam_status solve_impl(isam_plan* P, const T* s_d, const i
 isam_status validate(const isam_params* p) {
   if (!p) return ISAM_ERR_INVALID;
   const int nz = p->nz ? p->nz : p->nk;
-  if (!pow2(p->nx) || !pow2(p->ny) || !pow2(p->nk) || !pow2(nz)) return ISAM_ERR_INVALID;
+  int lg = 0, r3 = 0;
+  if (!fft_length(p->nx, &lg, &r3) || !fft_length(p->ny, &lg, &r3)) return ISAM_ERR_INVALID;
+  if (!pow2(p->nk) || !pow2(nz)) return ISAM_ERR_INVALID;
   if (p->nx > 4096 || p->ny > 4096) return ISAM_ERR_UNSUPPORTED;
   if (p->nk < 16 || nz < 16) return ISAM_ERR_UNSUPPORTED;
   if (nz < p->nk || nz > 2048) return ISAM_ERR_UNSUPPORTED;

@@ -18,12 +18,26 @@
 
 namespace isam {
 
-int lat_tile(int L, int M) {   // pair-columns per block
+int lat_tile(int L, int M) {   // pair-columns per block (a power of two)
   int tp = L >= 8 ? 4096 / L : 8;
   if (tp > 8) tp = 8;
   if (tp > M / 2) tp = M / 2;
   if (tp < 1) tp = 1;
+  while (tp & (tp - 1)) tp &= tp - 1;
   return tp;
+}
+
+bool fft_length(int L, int* log2, int* r3) {
+  if (L < 1) return false;
+  int t = 0, m = L;
+  if (m % 3 == 0) { m /= 3; t = 1; }
+  if (m & (m - 1)) return false;
+  int p = 0;
+  while ((1 << p) < m) ++p;
+  if (t && p < 3) return false;
+  *log2 = p;
+  *r3 = t;
+  return true;
 }
 
 // T_tau(u) = u max(|u| - tau, 0) / (max(|u| - tau, 0) + tau)  (Eq. 14),
@@ -59,7 +73,7 @@ __global__ void __launch_bounds__(512, 2) k_lat(const __grid_constant__ LatArgs<
   const int tid = threadIdx.x, nt = blockDim.x;
   const int TP = a.TZ, L = a.L, logTP = a.logTZ;
   cplx<T>* tw = reinterpret_cast<cplx<T>*>(buf + size_t(padded_rows(L)) * TP);
-  build_twiddles<T>(tw, L, a.logL);
+  build_twiddles<T>(tw, L, a.logL, a.r3);
   const int col = tid & (TP - 1), b = tid >> logTP;
   const size_t M = size_t(a.M);
   const size_t m_first = size_t(blockIdx.x) * (2 * TP);
@@ -96,9 +110,9 @@ __global__ void __launch_bounds__(512, 2) k_lat(const __grid_constant__ LatArgs<
   __syncthreads();
 
   if (MODE == LAT_C2C_FWD || MODE == LAT_R2C_FWD)
-    fft_smem<-1, false, T>(buf, TP, col, b, L, a.logL, tw, true);
+    fft_smem<-1, false, T>(buf, TP, col, b, L, a.logL, tw, true, a.r3);
   else
-    fft_smem<+1, false, T>(buf, TP, col, b, L, a.logL, tw, true);
+    fft_smem<+1, false, T>(buf, TP, col, b, L, a.logL, tw, true, a.r3);
 
   const T nrm = a.norm;
   if (MODE == LAT_C2C_FWD || MODE == LAT_C2C_INV || MODE == LAT_R2C_FWD) {
@@ -172,7 +186,7 @@ __global__ void __launch_bounds__(512, 2) k_lat(const __grid_constant__ LatArgs<
   }
   if (bad) atomicOr(a.flag, 1);
   __syncthreads();
-  fft_smem<-1, false, T>(buf, TP, col, b, L, a.logL, tw, true);
+  fft_smem<-1, false, T>(buf, TP, col, b, L, a.logL, tw, true, a.r3);
   C* out = static_cast<C*>(a.out);
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
@@ -202,11 +216,11 @@ __global__ void __launch_bounds__(512, 2) k_lat(const __grid_constant__ LatArgs<
   }
 }
 
-static int ilog2_host(int v) { int r = 0; while ((1 << r) < v) ++r; return r; }
-
 template <typename T> size_t lat_smem_bytes(int L, int TP) {
+  int lg = 0, r3 = 0;
+  fft_length(L, &lg, &r3);
   return size_t(padded_rows(L)) * TP * sizeof(cpair<T>) +
-         size_t(twiddle_entries(L, ilog2_host(L))) * sizeof(cplx<T>);
+         size_t(twiddle_entries(L, lg, r3)) * sizeof(cplx<T>);
 }
 
 template <typename T, int MODE>

@@ -94,7 +94,9 @@ def _params(isam, **kw):
 
 
 @pytest.mark.parametrize("field,value,status", [
-    ("nx", 3, 1),            # not a power of two
+    ("nx", 5, 1),            # neither 2^p nor 3 * 2^p
+    ("nx", 12, 1),           # 3 * 2^p needs p >= 3
+    ("ny", 40, 1),
     ("nk", 48, 1),
     ("nz", 16, 6),           # nz < nk
     ("nz", 4096, 6),         # beyond the 2048-row axial limit

@@ -59,6 +59,10 @@ CASES = [
     ("ascan_q0_2048", dict(nx=1, nk=2048, nz=2048)),
     ("volume_4x2x2048", dict(nx=4, ny=2, nk=2048, nz=2048)),
     ("bscan_4x1024_nz2048", dict(nx=4, nk=1024, nz=2048)),
+    # lateral sizes 3 * 2^p: radix-8/4/2 passes then one radix-3 pass
+    ("bscan_384x64_radix3", dict(nx=384, nk=64, nz=64)),
+    ("bscan_768x32_radix3", dict(nx=768, nk=32, nz=64)),
+    ("volume_24x24x32_radix3", dict(nx=24, ny=24, nk=32, nz=32)),
 ]
 
 

@@ -70,6 +70,20 @@ def test_fista_nz2048_matches_oracle(torch):
     plan.close()
 
 
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-3), ("fp64", 1e-6)])
+def test_fista_radix3_lateral_size(torch, prec, tol):
+    """nx = 96 = 3 * 32: the lateral passes end with a radix-3 pass."""
+    from paper_1905_06058_gb300.isam import Plan
+    wl, ref, s, L = problem(nx=96, nk=64, nz=64, seed=23)
+    lam = O.lambda_from_data(ref.adjoint, s, 0.05)
+    res = O.fista(ref.forward, ref.adjoint, s, lam, L, max_iter=40, shape=ref.image_shape)
+    plan = Plan(wl.geom, precision=prec)
+    dt = np.float64 if prec == "fp64" else np.float32
+    out, info = plan.solve(dev(torch, s, dt), lambda_abs=lam, L=L, max_iter=40)
+    assert rel(out.cpu().numpy(), res.eta) < tol
+    plan.close()
+
+
 def test_weighted_addback_and_lambda_rule(torch):
     """MBIR+ (depth weights 0.5 -> 1, residual added back, §3.1, §4.2)."""
     from paper_1905_06058_gb300.isam import Plan
