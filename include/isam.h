@@ -226,6 +226,31 @@ isam_status isam_fista_unrolled_vjp(isam_plan* plan, const void* s_d,
                                     const void* ckpt, const void* z_bar, void* s_bar,
                                     double* grad);
 
+/* ---- Batched solves as one CUDA graph --------------------------------------
+ * Many independent MBIR solves (Alg. 1), each with its own plan (geometry,
+ * dispersion, focus), data, lambda, L, weights and iteration count, recorded
+ * once into one CUDA graph; isam_batch_run replays the whole batch with one
+ * launch.  Each entry runs on its own forked stream, so entries overlap on
+ * the GPU; one entry is the same kernel sequence as isam_solve with tol = 0.
+ * Create: plans distinct, on one device, profiling off; opts[i].tol must be 0
+ * (the stop rule needs the host); L = 0 is estimated now (cached per plan);
+ * lambda_rel is evaluated on the device at every run from the s_d[i] contents
+ * then.  The batch keeps the pointers: plans, s_d[i] (device spectra) and
+ * eta_out[i] (device images) must stay valid, and the plans unused by other
+ * calls while a run is in flight.  Synchronous.  `stream` must not be the
+ * legacy default stream (capture is not allowed there); NULL makes the batch
+ * create its own.  Run: launches the graph on that stream, waits, and fills
+ * info[i] (nullable; rr = -1); returns the first non-OK entry status.  The
+ * caller orders earlier work on s_d before the run (e.g. synchronises). */
+typedef struct isam_batch isam_batch;
+isam_status isam_batch_create(isam_plan* const* plans, int32_t n, const void* const* s_d,
+                              const isam_solve_opts* opts, void* const* eta_out, void* stream,
+                              isam_batch** out);
+isam_status isam_batch_run(isam_batch* batch, isam_solve_info* info);
+/* Kernel launches recorded in the batch's graph (-1 for NULL). */
+int64_t isam_batch_kernel_count(const isam_batch* batch);
+void isam_batch_destroy(isam_batch* batch);
+
 /* Kernel launches issued by the last isam_forward / isam_adjoint / isam_solve. */
 int64_t isam_last_launch_count(const isam_plan* plan);
 

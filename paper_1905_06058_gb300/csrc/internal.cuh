@@ -80,6 +80,8 @@ template <typename T> struct LatArgs {
   double* partial;       // [gridDim.x*gridDim.y][3] norm partials, or null
   int* flag;             // non-finite flag
   cplx<T>* uout;         // optional: u^k = eta^k - g^k before the threshold
+  const double* lam_dev; // optional: lambda / L = lam_scale * (*lam_dev), read on the device
+  double lam_scale;
 };
 
 // Columns q and -q share the Stolt map; the axial kernels process them as a

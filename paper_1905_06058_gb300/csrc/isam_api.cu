@@ -374,7 +374,9 @@ template <typename T> isam_status fista_iteration(isam_plan* P, Impl<T>& im,
                                                   double L, double mu_prev, double mu,
                                                   bool norms, const cplx<T>* ehat_in = nullptr,
                                                   cplx<T>* ehat_out = nullptr,
-                                                  cplx<T>* u_out = nullptr) {
+                                                  cplx<T>* u_out = nullptr,
+                                                  const double* lam_dev = nullptr,
+                                                  double lam_scale = 0.0) {
   cudaStream_t s = P->stream;
   if (!ehat_in) ehat_in = im.eta_hat;
   if (!ehat_out) ehat_out = im.eta_hat;
@@ -389,6 +391,7 @@ template <typename T> isam_status fista_iteration(isam_plan* P, Impl<T>& im,
     u = lat_args<T>(1, P->ny, P->nx * P->nz, im.grad, ehat_out);
   }
   u.z1 = z1; u.z2 = z2; u.zout = zout; u.w = w; u.nz = P->nz; u.uout = u_out;
+  u.lam_dev = lam_dev; u.lam_scale = lam_scale;
   u.inv_L = T(1.0 / L); u.lam_over_L = T(lam / L); u.mu_prev = T(mu_prev); u.mu = T(mu);
   u.partial = norms ? P->partial : nullptr;
   u.flag = P->flag;
@@ -1217,3 +1220,236 @@ isam_status isam_dispersion_compensated_ifft(isam_plan* P, const void* s_d, void
 
 }  // extern "C"
 
+
+// ----------------------------------------------------------------------------
+// Batched solves recorded as one CUDA graph
+// ----------------------------------------------------------------------------
+struct isam_batch {
+  int n = 0;
+  int device = 0;
+  std::vector<isam_plan*> plans;
+  std::vector<isam_solve_opts> opts;
+  std::vector<double> L;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> joins;
+  cudaEvent_t fork = nullptr;
+  cudaStream_t origin = nullptr;
+  bool own_origin = false;      // created here (capture cannot use the legacy stream)
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int64_t kernels = 0;   // kernel launches recorded in the graph
+};
+
+namespace {
+
+// Everything a recorded solve needs that cannot happen during capture:
+// workspace allocation and the Lipschitz constant (cached per plan).
+template <typename T> isam_status batch_prepare(isam_plan* P, const isam_solve_opts* o,
+                                                double* L_out) {
+  Impl<T>& im = impl_of<T>(P);
+  if (!im.zA) ISAM_TRY(dalloc(&im.zA, P->n_img));
+  if (!im.zB) ISAM_TRY(dalloc(&im.zB, P->n_img));
+  if (!im.sdh) ISAM_TRY(dalloc(&im.sdh, P->n_spec));
+  if (!im.s_tmp) ISAM_TRY(dalloc(&im.s_tmp, P->n_spec));
+  double L = o->L;
+  if (!(L > 0)) {
+    if (!(P->L_cache > 0)) {
+      double Lc = 0.0;
+      if (precision_fits<double>(P))
+        ISAM_TRY(power_iteration<double>(P, kPowerIters, kPowerRtol, nullptr, 0, &Lc));
+      else
+        ISAM_TRY(power_iteration<T>(P, kPowerIters, kPowerRtol, nullptr, 0, &Lc));
+      P->L_cache = Lc;
+    }
+    L = P->L_cache;
+  }
+  if (!(L > 0)) return ISAM_ERR_INVALID;
+  *L_out = L;
+  return ISAM_OK;
+}
+
+// One whole solve on the plan's stream with no host synchronisation: the
+// relative lambda = c ||A^H s_d||_inf stays on the device (the update kernel
+// reads it), so a recorded graph stays correct when s_d's contents change.
+template <typename T> isam_status batch_enqueue(isam_plan* P, const T* s_d,
+                                                const isam_solve_opts* o, double L,
+                                                cplx<T>* eta_out) {
+  Impl<T>& im = impl_of<T>(P);
+  cudaStream_t s = P->stream;
+  const size_t bytes = sizeof(cplx<T>) * P->n_img;
+  CUDA_TRY(cudaMemsetAsync(P->flag, 0, sizeof(int), s));
+  ISAM_TRY(lat_forward<T>(P, im, s_d, im.sdh, P->nk, true));
+  const double lam = o->lambda_abs;
+  const double* lam_dev = nullptr;
+  double lam_scale = 0.0;
+  if (!(lam > 0)) {
+    ISAM_TRY(op_adjoint<T>(P, s_d, im.zA));
+    ISAM_TRY(launch(P, ISAM_KCLASS_MISC, [&] {
+      return launch_max_abs<T>(im.zA, P->n_img, P->partial, RED_BLOCKS, P->dscal, s);
+    }));
+    lam_dev = P->dscal;
+    lam_scale = o->lambda_rel / L;
+  }
+  CUDA_TRY(cudaMemsetAsync(im.zA, 0, bytes, s));
+  CUDA_TRY(cudaMemsetAsync(im.zB, 0, bytes, s));
+  CUDA_TRY(cudaMemsetAsync(im.eta_hat, 0, bytes, s));
+  std::vector<double> mu;
+  momentum(o->max_iter + 1, mu);
+  cplx<T>* zP = im.zA;
+  cplx<T>* zQ = im.zB;
+  const T* w = static_cast<const T*>(o->w_dev);
+  for (int k = 1; k <= o->max_iter; ++k) {
+    ISAM_TRY(fista_iteration<T>(P, im, zP, zQ, zQ, w, lam, L, mu[k - 1], mu[k], false, nullptr,
+                                nullptr, nullptr, lam_dev, lam_scale));
+    std::swap(zP, zQ);
+  }
+  if (o->residual_addback) {
+    ISAM_TRY(op_forward<T>(P, zP, im.s_tmp));
+    ISAM_TRY(launch(P, ISAM_KCLASS_MISC, [&] {
+      return launch_rsub<T>(s_d, im.s_tmp, im.s_tmp, P->n_spec, s);
+    }));
+    ISAM_TRY(op_adjoint<T>(P, im.s_tmp, im.grad));
+    ISAM_TRY(launch(P, ISAM_KCLASS_MISC, [&] {
+      return launch_caxpy<T>(zP, im.grad, T(1.0 / L), eta_out, P->n_img, s);
+    }));
+  } else {
+    CUDA_TRY(cudaMemcpyAsync(eta_out, zP, bytes, cudaMemcpyDeviceToDevice, s));
+  }
+  return ISAM_OK;
+}
+
+void batch_free(isam_batch* B) {
+  if (!B) return;
+  if (B->exec) cudaGraphExecDestroy(B->exec);
+  if (B->graph) cudaGraphDestroy(B->graph);
+  for (cudaStream_t st : B->streams) cudaStreamDestroy(st);
+  for (cudaEvent_t e : B->joins) cudaEventDestroy(e);
+  if (B->fork) cudaEventDestroy(B->fork);
+  if (B->own_origin && B->origin) cudaStreamDestroy(B->origin);
+  delete B;
+}
+
+}  // namespace
+
+extern "C" {
+
+isam_status isam_batch_create(isam_plan* const* plans, int32_t n, const void* const* s_d,
+                              const isam_solve_opts* opts, void* const* eta_out, void* stream,
+                              isam_batch** out) {
+  if (!out) return ISAM_ERR_INVALID;
+  *out = nullptr;
+  if (!plans || n < 1 || !s_d || !opts || !eta_out) return ISAM_ERR_INVALID;
+  for (int i = 0; i < n; ++i) {
+    if (!plans[i] || !s_d[i] || !eta_out[i]) return ISAM_ERR_INVALID;
+    ISAM_TRY(check_opts(plans[i], &opts[i]));
+    if (opts[i].tol != 0.0) return ISAM_ERR_INVALID;       // no host stop rule in a graph
+    if (plans[i]->prof || plans[i]->device != plans[0]->device) return ISAM_ERR_INVALID;
+    for (int j = 0; j < i; ++j)
+      if (plans[j] == plans[i]) return ISAM_ERR_INVALID;
+  }
+  DeviceGuard g(plans[0]->device);
+  isam_batch* B = new isam_batch();
+  B->n = n;
+  B->device = plans[0]->device;
+  B->origin = static_cast<cudaStream_t>(stream);
+  B->plans.assign(plans, plans + n);
+  B->opts.assign(opts, opts + n);
+  B->L.assign(n, 0.0);
+  isam_status st = ISAM_OK;
+  for (int i = 0; i < n && st == ISAM_OK; ++i) {
+    isam_plan* P = plans[i];
+    st = P->p.precision == ISAM_FP64 ? batch_prepare<double>(P, &opts[i], &B->L[i])
+                                     : batch_prepare<float>(P, &opts[i], &B->L[i]);
+    if (st == ISAM_OK) st = from_cuda(cudaStreamSynchronize(P->stream));
+  }
+  if (st == ISAM_OK && !B->origin) {
+    st = from_cuda(cudaStreamCreateWithFlags(&B->origin, cudaStreamNonBlocking));
+    B->own_origin = st == ISAM_OK;
+  }
+  if (st == ISAM_OK) st = from_cuda(cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming));
+  for (int i = 0; i < n && st == ISAM_OK; ++i) {
+    cudaStream_t sx = nullptr;
+    cudaEvent_t ev = nullptr;
+    st = from_cuda(cudaStreamCreateWithFlags(&sx, cudaStreamNonBlocking));
+    if (st == ISAM_OK) B->streams.push_back(sx);
+    if (st == ISAM_OK) st = from_cuda(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    if (st == ISAM_OK) B->joins.push_back(ev);
+  }
+  if (st != ISAM_OK) {
+    batch_free(B);
+    return st;
+  }
+  // record: fork every entry onto its own stream, join them back
+  st = from_cuda(cudaStreamBeginCapture(B->origin, cudaStreamCaptureModeRelaxed));
+  if (st == ISAM_OK) st = from_cuda(cudaEventRecord(B->fork, B->origin));
+  for (int i = 0; i < n && st == ISAM_OK; ++i) {
+    isam_plan* P = plans[i];
+    cudaStream_t saved = P->stream;
+    const int64_t l0 = P->launches;
+    P->stream = B->streams[i];
+    st = from_cuda(cudaStreamWaitEvent(P->stream, B->fork, 0));
+    if (st == ISAM_OK)
+      st = P->p.precision == ISAM_FP64
+               ? batch_enqueue<double>(P, static_cast<const double*>(s_d[i]), &opts[i], B->L[i],
+                                       static_cast<double2*>(eta_out[i]))
+               : batch_enqueue<float>(P, static_cast<const float*>(s_d[i]), &opts[i], B->L[i],
+                                      static_cast<float2*>(eta_out[i]));
+    if (st == ISAM_OK) st = from_cuda(cudaEventRecord(B->joins[i], P->stream));
+    if (st == ISAM_OK) st = from_cuda(cudaStreamWaitEvent(B->origin, B->joins[i], 0));
+    B->kernels += P->launches - l0;
+    P->stream = saved;
+  }
+  cudaGraph_t graph = nullptr;
+  const isam_status end = from_cuda(cudaStreamEndCapture(B->origin, &graph));
+  B->graph = graph;
+  if (st == ISAM_OK) st = end;
+  if (st == ISAM_OK) st = from_cuda(cudaGraphInstantiate(&B->exec, B->graph, 0));
+  if (st != ISAM_OK) {
+    cudaGetLastError();
+    batch_free(B);
+    return st;
+  }
+  *out = B;
+  return ISAM_OK;
+}
+
+isam_status isam_batch_run(isam_batch* B, isam_solve_info* info) {
+  if (!B) return ISAM_ERR_INVALID;
+  DeviceGuard g(B->device);
+  CUDA_TRY(cudaGraphLaunch(B->exec, B->origin));
+  CUDA_TRY(cudaStreamSynchronize(B->origin));
+  isam_status first = ISAM_OK;
+  for (int i = 0; i < B->n; ++i) {
+    isam_plan* P = B->plans[i];
+    int flag = 0;
+    double m = 0.0;
+    CUDA_TRY(cudaMemcpy(&flag, P->flag, sizeof(int), cudaMemcpyDeviceToHost));
+    const isam_solve_opts& o = B->opts[i];
+    double lam = o.lambda_abs;
+    if (!(lam > 0)) {
+      CUDA_TRY(cudaMemcpy(&m, P->dscal, sizeof(double), cudaMemcpyDeviceToHost));
+      lam = o.lambda_rel * m;
+    }
+    const isam_status st = flag ? ISAM_ERR_NONFINITE : ISAM_OK;
+    if (st != ISAM_OK && first == ISAM_OK) first = st;
+    if (info) {
+      info[i].iterations = o.max_iter;
+      info[i].rr = -1.0;
+      info[i].lambda = lam;
+      info[i].L = B->L[i];
+      info[i].status = st;
+    }
+  }
+  return first;
+}
+
+int64_t isam_batch_kernel_count(const isam_batch* B) { return B ? B->kernels : -1; }
+
+void isam_batch_destroy(isam_batch* B) {
+  if (!B) return;
+  DeviceGuard g(B->device);
+  cudaStreamSynchronize(B->origin);
+  batch_free(B);
+}
+
+}  // extern "C"

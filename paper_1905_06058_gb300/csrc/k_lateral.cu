@@ -143,6 +143,7 @@ __global__ void __launch_bounds__(512, 2) k_lat(const __grid_constant__ LatArgs<
   double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
   bool bad = false;
   const T sg = nrm * a.inv_L;
+  const T lam_over_L = a.lam_dev ? T(a.lam_scale * *a.lam_dev) : a.lam_over_L;
 #pragma unroll
   for (int h = 0; h < 8; h += 4) {
     V z1v[4], z2v[4];
@@ -162,8 +163,8 @@ __global__ void __launch_bounds__(512, 2) k_lat(const __grid_constant__ LatArgs<
       const V g = escale(buf[sidx(e)], sg);                 // g^k = (1/L) A^H(A eta - s)
       const V z1 = z1v[i];
       const V eta = eadd(z1, escale(esub(z1, z2v[i]), a.mu_prev));
-      const T tau0 = a.w ? a.lam_over_L * a.w[n0] : a.lam_over_L;
-      const T tau1 = a.w ? a.lam_over_L * a.w[n0 + 1] : a.lam_over_L;
+      const T tau0 = a.w ? lam_over_L * a.w[n0] : lam_over_L;
+      const T tau1 = a.w ? lam_over_L * a.w[n0 + 1] : lam_over_L;
       const V u = esub(eta, g);
       if (a.uout) *reinterpret_cast<V*>(a.uout + gi) = u;
       V z;

@@ -77,6 +77,12 @@ _SIGS = {
                                          ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]),
     "isam_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "isam_dispersion_compensated_ifft": (ctypes.c_int, [_P, _P, _P]),
+    "isam_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, ctypes.POINTER(_P),
+                                         ctypes.POINTER(SolveOpts), ctypes.POINTER(_P), _P,
+                                         ctypes.POINTER(_P)]),
+    "isam_batch_run": (ctypes.c_int, [_P, ctypes.POINTER(SolveInfo)]),
+    "isam_batch_kernel_count": (ctypes.c_int64, [_P]),
+    "isam_batch_destroy": (None, [_P]),
     "isam_set_model": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                       ctypes.c_double]),
     "isam_param_grad": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
@@ -364,3 +370,61 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class Batch:
+    """isam_batch_create / isam_batch_run: independent solves of several plans
+    recorded once as one CUDA graph and replayed with one launch.
+
+    ``entries`` is a list of (plan, s_d, out, solve keyword dict); the keywords
+    are those of Plan.solve (lambda_rel, lambda_abs, max_iter, w, addback, L).
+    The tensors are kept referenced by the batch."""
+
+    def __init__(self, entries, stream=None):
+        self._h = None
+        n = len(entries)
+        self._keep = []
+        plans = (_P * n)()
+        sds = (_P * n)()
+        outs = (_P * n)()
+        opts = (SolveOpts * n)()
+        for i, (plan, s, out, kw) in enumerate(entries):
+            plan._sync_stream()
+            plans[i] = plan._h
+            sds[i] = plan._dev(s, plan.real_dtype, plan.spec_shape, "s_d")
+            outs[i] = plan._dev(out, plan.cplx_dtype, plan.image_shape, "out")
+            opts[i] = plan._opts(kw.get("lambda_rel", 0.01), kw.get("lambda_abs", 0.0),
+                                 kw.get("max_iter", 100), 0.0, 1, kw.get("w"),
+                                 kw.get("addback", False), kw.get("L", 0.0), 0.0)
+            self._keep.append((plan, s, out, kw.get("w")))
+        self.n = n
+        h = _P()
+        sh = None if stream is None else _P(int(stream.cuda_stream))
+        _check(_lib.isam_batch_create(plans, n, sds, opts, outs, sh, ctypes.byref(h)),
+               "isam_batch_create")
+        self._h = h
+
+    def run(self):
+        import torch
+        torch.cuda.current_stream().synchronize()
+        infos = (SolveInfo * self.n)()
+        st = _lib.isam_batch_run(self._h, infos)
+        if st not in (0, 4):            # a non-finite entry is reported in its info
+            _check(st, "isam_batch_run")
+        return [dict(iterations=f.iterations, rr=f.rr, lam=f.lambda_, L=f.L, status=f.status)
+                for f in infos]
+
+    def kernel_count(self) -> int:
+        return int(_lib.isam_batch_kernel_count(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.isam_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
