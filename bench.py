@@ -44,6 +44,8 @@ def parse_args():
     ap.add_argument("--no-extras", action="store_true", help="skip A+A^H, FP64 and volume lines")
     ap.add_argument("--volume", action="store_true", help="also time the 256^2 x 2048 volume")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-batch", action="store_true", help="skip the 96-B-scan batch line")
+    ap.add_argument("--batch-iters", type=int, default=200)
     ap.add_argument("--calib-steps", type=int, default=10,
                     help="Adam steps timed in the calibration line")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
@@ -368,6 +370,8 @@ def run_extras(torch, plan, s_d, wl, args, L):
     p64.close()
     ex["cufft_comparison_us"] = cufft_comparison(torch, plan)
     ex["calibration"] = run_calibration(torch, args.calib_steps)
+    if not args.no_batch:
+        ex["batch"] = run_batch(torch, args.batch_iters)
     if args.volume:
         ex["volume"] = run_volume(torch)
     return ex
@@ -432,6 +436,55 @@ def run_calibration(torch, steps: int):
             "loss_first": res.losses[0], "loss_last": res.losses[-1],
             "theta_error_start_a2_a3_z0": err(wl.start), "theta_error_end_a2_a3_z0": err(res.theta),
             "units": "a_i: rad at the band edge; z0: fraction of the depth range"}
+
+
+def run_batch(torch, iters: int):
+    """96 B-scans of uneven size (Nx 256..1024, Nk 1024/2048, own NA, dispersion,
+    focus and lambda), `iters` FISTA iterations each, recorded as one CUDA graph
+    and replayed with one launch; against the same solves issued one after
+    another through isam_solve.  Spectra come from each plan's own model plus
+    30 dB noise; L from 50 power iterations (x 1.01)."""
+    import time
+    from paper_1905_06058_gb300 import inputs as I
+    from paper_1905_06058_gb300.isam import Batch, Plan
+    t_setup = time.perf_counter()
+    ents = []
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(4)
+    for e in I.config4():
+        plan = Plan(e.geom)
+        s = plan.forward(torch.from_numpy(I.batch_specimen(e)).cuda())
+        sigma = float(torch.linalg.vector_norm(s)) / (s.numel() ** 0.5 * 10 ** 1.5)
+        s = s + sigma * torch.randn(s.shape, generator=gen, device="cuda")
+        L = 1.01 * plan.lipschitz(iters=50, rtol=1e-6)
+        out = torch.empty(plan.image_shape, dtype=torch.complex64, device="cuda")
+        ents.append((plan, s, out, dict(lambda_rel=e.lambda_rel, max_iter=iters, L=L)))
+    b = Batch(ents)
+    setup_s = time.perf_counter() - t_setup
+    b.run()                                               # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    infos = b.run()
+    t_graph = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for plan, s, out, kw in ents:
+        plan.solve(s, out=out, **kw)
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    total = iters * len(ents)
+    work = sum(p.geom.nx * p.geom.nk for p, *_ in ents) / (1024 * 2048)
+    res = {"workload": f"{len(ents)} B-scans, Nx 256..1024, Nk 1024/2048",
+           "iters_each": iters, "graph_kernels": b.kernel_count(),
+           "graph_s": t_graph, "graph_iters_per_s": total / t_graph,
+           "sequential_solve_s": t_seq, "sequential_iters_per_s": total / t_seq,
+           "per_solve_latency_s": t_graph,
+           "bscan_1024x2048_equivalents": work,
+           "statuses_ok": sum(1 for i in infos if i["status"] == 0), "setup_s": setup_s}
+    b.close()
+    for plan, *_ in ents:
+        plan.close()
+    return res
 
 
 def run_volume(torch):

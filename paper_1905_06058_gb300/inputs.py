@@ -283,6 +283,40 @@ def config5(n_bscans: int = 16, nx: int = 512, nk: int = 2048) -> CalibWorkload:
     return CalibWorkload(f"calib_{n_bscans}x{nx}x{nk}", g, etas, start, 30.0, 0.01, 20, 5)
 
 
+@dataclasses.dataclass
+class BatchEntry:
+    """One B-scan of an uneven batch: its geometry and how its specimen is drawn."""
+
+    geom: Geometry
+    seed: int
+    sparsity: float          # fraction of speckle pixels
+    lambda_rel: float
+
+
+def config4(n: int = 96) -> list:
+    """96 B-scans of uneven size for one batched launch: Nx from {256, 384,
+    512, 768, 1024}, Nk = nz from {1024, 2048}, NA U[0.08, 0.2], focus at
+    U[0.2, 0.8] of the range, own dispersion (as draw_dispersion), speckle
+    sparsity U[1%, 3%] plus 2 interfaces and 50 points, lambda_rel
+    U[0.005, 0.02], 30 dB noise; 200 iterations each."""
+    seed = SEED_BASE + 4
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        nx = int(rng.choice([256, 384, 512, 768, 1024]))
+        nk = int(rng.choice([1024, 2048]))
+        g = _geometry(nx, 1, nk, nk, float(rng.uniform(0.08, 0.2)), float(rng.uniform(0.2, 0.8)),
+                      rng)
+        out.append(BatchEntry(g, seed + 100 + i, float(rng.uniform(0.01, 0.03)),
+                              float(rng.uniform(0.005, 0.02))))
+    return out
+
+
+def batch_specimen(e: BatchEntry, dtype=np.complex64) -> np.ndarray:
+    rng = np.random.default_rng(e.seed)
+    return layered_specimen(rng, (1, e.geom.nx, e.geom.nz), 2, e.sparsity, 50, dtype)
+
+
 def small_bscan(nx=32, nk=64, nz=0, na=0.1, focus_frac=0.3, n_points=6, seed=7,
                 dispersion=True, dx_scale=1.0, min_sep=0, ny=1) -> Workload:
     """Small seeded case for parity tests (several tiles and a ragged tail)."""
