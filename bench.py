@@ -223,6 +223,7 @@ def run_ours(args):
     g = wl.geom
     plan = Plan(g, precision="fp32")
     s_d, _ = make_problem(torch, plan, wl, wl.seed + rank)
+    tuned = plan.autotune()                     # launch shapes timed on this plan
     out = torch.empty(plan.image_shape, dtype=torch.complex64, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     opts = dict(lambda_rel=wl.lambda_rel, max_iter=args.iters, tol=1e-12, check_every=CHECK_EVERY,
@@ -322,7 +323,8 @@ def run_ours(args):
                            "nz": 2048, "iters_per_step": args.iters, "nufft_J": 6,
                            "lambda_rel": wl.lambda_rel, "check_every": CHECK_EVERY,
                            "l2": "flushed between timed steps (256 MiB write)",
-                           "parallelism": f"replicas x{world}"},
+                           "parallelism": f"replicas x{world}",
+                           "autotuned": tuned},
                 "gpu_launches": launches, "clocks": clk, "e2e": e2e, "roofline": roofline,
                 "cpu_baseline": cpu,
                 "iteration_gbs_algorithmic": iter_gbs,
@@ -440,7 +442,8 @@ def run_calibration(torch, steps: int):
 
 def run_batch(torch, iters: int):
     """96 B-scans of uneven size (Nx 256..1024, Nk 1024/2048, own NA, dispersion,
-    focus and lambda), `iters` FISTA iterations each, recorded as one CUDA graph
+    focus and lambda), each plan autotuned (isam_autotune), `iters` FISTA
+    iterations each, recorded as one CUDA graph
     and replayed with one launch; against the same solves issued one after
     another through isam_solve.  Spectra come from each plan's own model plus
     30 dB noise; L from 50 power iterations (x 1.01)."""
@@ -457,6 +460,7 @@ def run_batch(torch, iters: int):
         sigma = float(torch.linalg.vector_norm(s)) / (s.numel() ** 0.5 * 10 ** 1.5)
         s = s + sigma * torch.randn(s.shape, generator=gen, device="cuda")
         L = 1.01 * plan.lipschitz(iters=50, rtol=1e-6)
+        plan.autotune()
         out = torch.empty(plan.image_shape, dtype=torch.complex64, device="cuda")
         ents.append((plan, s, out, dict(lambda_rel=e.lambda_rel, max_iter=iters, L=L)))
     b = Batch(ents)

@@ -251,6 +251,16 @@ isam_status isam_batch_run(isam_batch* batch, isam_solve_info* info);
 int64_t isam_batch_kernel_count(const isam_batch* batch);
 void isam_batch_destroy(isam_batch* batch);
 
+/* Pick launch shapes by timing the plan's own FISTA iteration (CUDA events on
+ * the plan's stream, zero data, 10 timed iterations per candidate): the
+ * lateral-update tile width (1, 2, 4 or 8 pairs of depth columns per block,
+ * where they fit) and, when the plan holds a Stolt table, table lookups versus
+ * on-the-fly Stolt positions.  Neither choice changes any column's arithmetic.
+ * The fastest is kept in the plan and used by later calls; *tile and
+ * *stolt_table (nullable) receive it.  Overwrites the plan's workspace.
+ * Synchronous. */
+isam_status isam_autotune(isam_plan* plan, int32_t* tile, int32_t* stolt_table);
+
 /* Kernel launches issued by the last isam_forward / isam_adjoint / isam_solve. */
 int64_t isam_last_launch_count(const isam_plan* plan);
 

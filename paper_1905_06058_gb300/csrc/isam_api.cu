@@ -64,6 +64,10 @@ struct isam_plan {
   double* hscal = nullptr;      // pinned host mirror [8]
   int* flag = nullptr;          // device non-finite flag
   double L_cache = 0.0;
+  // autotuned choices (0: the built-in heuristics): lateral update tile width
+  // and whether the fused kernel reads the Stolt table (1) or evaluates (2)
+  int tune_tp = 0;
+  int tune_table = 0;
   double* cpartial = nullptr;   // [npairs][5] calibration partial sums
   int64_t launches = 0;
   size_t n_img = 0, n_spec = 0;
@@ -262,6 +266,7 @@ template <typename T> AxArgs<T> ax_args(isam_plan* P, const Impl<T>& im, const c
   a.in = in; a.out = out; a.sc = P->sc; a.tab = im.tab;
   a.poly = poly_of<T>(P);
   a.pairs = P->pairs;
+  if (P->tune_table == 2) a.tab.stab = nullptr;
   return a;
 }
 
@@ -389,6 +394,10 @@ template <typename T> isam_status fista_iteration(isam_plan* P, Impl<T>& im,
   } else {
     ISAM_TRY(lat<T>(P, LAT_C2C_INV, lat_args<T>(P->ny, P->nx, P->nz, im.grad, im.grad)));
     u = lat_args<T>(1, P->ny, P->nx * P->nz, im.grad, ehat_out);
+  }
+  if (P->tune_tp) {
+    u.TZ = P->tune_tp;
+    u.logTZ = ilog2(P->tune_tp);
   }
   u.z1 = z1; u.z2 = z2; u.zout = zout; u.w = w; u.nz = P->nz; u.uout = u_out;
   u.lam_dev = lam_dev; u.lam_scale = lam_scale;
@@ -725,7 +734,7 @@ isam_status isam_plan_create(const isam_params* p, void* stream, isam_plan** out
     const int L = P->ny == 1 ? P->nx : P->ny;
     const int M = P->ny == 1 ? P->nz : P->nx * P->nz;
     const int npairs_max = P->nx * P->ny / 2 + 4;
-    P->n_partial = std::max(std::max(RED_BLOCKS, M / (2 * lat_tile(L, M))), npairs_max);
+    P->n_partial = std::max(std::max(RED_BLOCKS, M / 2), npairs_max);   // any update tile
   }
   if (st == ISAM_OK) st = dalloc(&P->partial, size_t(P->n_partial) * 3);
   if (st == ISAM_OK) st = dalloc(&P->dscal, 8);
@@ -1453,3 +1462,88 @@ void isam_batch_destroy(isam_batch* B) {
 }
 
 }  // extern "C"
+
+// ----------------------------------------------------------------------------
+// Autotuning of launch shapes on the plan's own workload
+// ----------------------------------------------------------------------------
+namespace {
+
+// Device time of `reps` FISTA iterations (after 2 untimed ones) on zero data:
+// the kernels' work does not depend on the values.
+template <typename T> isam_status time_iterations(isam_plan* P, int reps, float* ms) {
+  Impl<T>& im = impl_of<T>(P);
+  cudaStream_t s = P->stream;
+  const size_t bytes = sizeof(cplx<T>) * P->n_img;
+  CUDA_TRY(cudaMemsetAsync(im.zA, 0, bytes, s));
+  CUDA_TRY(cudaMemsetAsync(im.zB, 0, bytes, s));
+  CUDA_TRY(cudaMemsetAsync(im.eta_hat, 0, bytes, s));
+  CUDA_TRY(cudaMemsetAsync(im.sdh, 0, sizeof(cplx<T>) * P->n_spec, s));
+  cudaEvent_t a = nullptr, b = nullptr;
+  CUDA_TRY(cudaEventCreate(&a));
+  CUDA_TRY(cudaEventCreate(&b));
+  isam_status st = ISAM_OK;
+  for (int i = 0; i < reps + 2 && st == ISAM_OK; ++i) {
+    if (i == 2) cudaEventRecord(a, s);
+    st = fista_iteration<T>(P, im, im.zA, im.zB, im.zB, nullptr, 1.0, 1.0, 0.5, 0.5, false);
+  }
+  cudaEventRecord(b, s);
+  if (st == ISAM_OK) st = from_cuda(cudaEventSynchronize(b));
+  if (st == ISAM_OK) st = from_cuda(cudaEventElapsedTime(ms, a, b));
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  harvest_events(P);
+  return st;
+}
+
+template <typename T> isam_status autotune_impl(isam_plan* P, int32_t* tile, int32_t* table) {
+  Impl<T>& im = impl_of<T>(P);
+  if (!im.zA) ISAM_TRY(dalloc(&im.zA, P->n_img));
+  if (!im.zB) ISAM_TRY(dalloc(&im.zB, P->n_img));
+  if (!im.sdh) ISAM_TRY(dalloc(&im.sdh, P->n_spec));
+  const int L = P->ny == 1 ? P->nx : P->ny;
+  const int M = P->ny == 1 ? P->nz : P->nx * P->nz;
+  const int threads_per_tp = L >= 8 ? L / 8 : 1;
+  const bool prof = P->prof;
+  P->prof = false;
+  const int reps = 10;
+  float best = 0.0f;
+  int best_tp = 0, best_tab = 0;
+  const int tabs[2] = {1, 2};
+  const int ntab = im.tab.stab ? 2 : 1;
+  isam_status st = ISAM_OK;
+  for (int it = 0; it < ntab && st == ISAM_OK; ++it) {
+    for (int tp = 1; tp <= 8 && st == ISAM_OK; tp *= 2) {
+      if (tp > M / 2 || threads_per_tp * tp > 512) continue;
+      P->tune_tp = tp;
+      P->tune_table = im.tab.stab ? tabs[it] : 0;
+      float ms = 0.0f;
+      st = time_iterations<T>(P, reps, &ms);
+      if (st == ISAM_OK && (best_tp == 0 || ms < best)) {
+        best = ms;
+        best_tp = tp;
+        best_tab = P->tune_table;
+      }
+    }
+  }
+  P->prof = prof;
+  P->tune_tp = st == ISAM_OK ? best_tp : 0;
+  P->tune_table = st == ISAM_OK ? best_tab : 0;
+  if (tile) *tile = P->tune_tp;
+  if (table) *table = P->tune_table == 2 ? 0 : (im.tab.stab ? 1 : 0);
+  return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+isam_status isam_autotune(isam_plan* P, int32_t* tile, int32_t* stolt_table) {
+  if (!P) return ISAM_ERR_INVALID;
+  DeviceGuard g(P->device);
+  P->launches = 0;
+  if (P->p.precision == ISAM_FP64) return autotune_impl<double>(P, tile, stolt_table);
+  return autotune_impl<float>(P, tile, stolt_table);
+}
+
+}  // extern "C"
+

@@ -81,6 +81,8 @@ _SIGS = {
                                          ctypes.POINTER(SolveOpts), ctypes.POINTER(_P), _P,
                                          ctypes.POINTER(_P)]),
     "isam_batch_run": (ctypes.c_int, [_P, ctypes.POINTER(SolveInfo)]),
+    "isam_autotune": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32),
+                                     ctypes.POINTER(ctypes.c_int32)]),
     "isam_batch_kernel_count": (ctypes.c_int64, [_P]),
     "isam_batch_destroy": (None, [_P]),
     "isam_set_model": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
@@ -352,6 +354,14 @@ class Plan:
             self._dev(z_bar, self.cplx_dtype, self.image_shape, "z_bar"),
             None if sb is None else _P(sb.data_ptr()), g), "isam_fista_unrolled_vjp")
         return np.array(g[:], dtype=np.float64), sb
+
+    def autotune(self) -> dict:
+        """isam_autotune: time the plan's own iteration and keep the fastest shapes."""
+        self._sync_stream()
+        tile, tab = ctypes.c_int32(), ctypes.c_int32()
+        _check(_lib.isam_autotune(self._h, ctypes.byref(tile), ctypes.byref(tab)),
+               "isam_autotune")
+        return {"lateral_tile": tile.value, "stolt_table": bool(tab.value)}
 
     def max_abs(self, eta) -> float:
         self._sync_stream()
