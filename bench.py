@@ -173,10 +173,9 @@ def algorithmic_bytes(cls: str, n_img: int, n_spec: int, real_bytes=4) -> int:
             "lat_update": c * n_img * 5}.get(cls)    # G, z1, z2 in; z, eta_hat out
 
 
-# DRAM bytes per launch from ncu captures of the current kernels (profiles/);
-# None where no capture of the current kernel exists.
 # DRAM bytes (read + write) per launch of the current kernels, from the ncu
-# captures summarised in profiles/ (caches flushed before each replayed launch)
+# captures summarised in profiles/ (caches flushed before each replayed
+# launch); a kernel without a capture of its current code is left out (None).
 NCU_TRAFFIC = {"ax_fused": 42382080, "lat_update": 51135744}
 
 
