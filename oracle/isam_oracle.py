@@ -20,6 +20,7 @@ What it computes (paper section / equation in brackets):
 * weighted complex soft threshold [Eq. 14], relative residual [Eq. 15],
   FISTA [Alg. 1], residual add-back [Alg. 1, optional last step];
 * Lipschitz constant of the gradient by power iteration;
+* the optional filter B(q, k) of Eq. 3 (b of Eq. 16), as a table over |q|;
 * the 1-D per-A-scan model of the DEFR objective (Eq. 10) and the
   dispersion-compensated IFFT (Eq. 9);
 * derivatives for calibrating the dispersion coefficients a_1..a_4 (Eq. 7)
@@ -250,16 +251,31 @@ def nufft_adjoint_column(y: np.ndarray, p: np.ndarray, interp: MinMaxInterpolato
 # ----------------------------------------------------------------------------
 
 
-class IsamOracle:
-    """A = Re o diag(e^{j phi}) o K and A^H for one geometry  [Eq. 12-13, 16-17]."""
+def expand_filter(g, table: np.ndarray) -> np.ndarray:
+    """The filter B(q, k) of Eq. 3 on every lateral-frequency column, [ny, nx, nk],
+    from a table over |q| classes, [ny//2 + 1, nx//2 + 1, nk]: column (iy, ix)
+    takes row (|my|, |mx|) with m the signed FFT index (B symmetric in q)."""
+    ny, nx = g.ny, g.nx
+    my = np.abs(np.fft.fftfreq(ny, 1.0 / ny).astype(int)) if ny > 1 else np.zeros(1, int)
+    mx = np.abs(np.fft.fftfreq(nx, 1.0 / nx).astype(int))
+    return table[my[:, None], mx[None, :], :]
 
-    def __init__(self, g, mode: str = "nufft", J: int = 6):
+
+class IsamOracle:
+    """A = Re o diag(e^{j phi}) o K and A^H for one geometry  [Eq. 12-13, 16-17].
+
+    ``filt`` (optional): the filter B of Eq. 3 as a table over |q| classes
+    (see expand_filter); S = B . e^{j phi} e^{j(2k+beta)z0} . H (b of Eq. 16)."""
+
+    def __init__(self, g, mode: str = "nufft", J: int = 6, filt: Optional[np.ndarray] = None):
         if mode not in ("exact", "nufft"):
             raise ValueError(mode)
         self.g, self.mode, self.J = g, mode, J
         self.grid = make_grid(g)
         gr = self.grid
         self.phase = spectral_phase(g, gr)                         # [ny,nx,nk]
+        if filt is not None:
+            self.phase = self.phase * expand_filter(g, filt)
         self.beta, self.prop = stolt_beta(gr.q2[..., None], gr.k[None, None, :])
         self.K = 2 * gr.nz
         self.interp = MinMaxInterpolator(gr.nz, self.K, J) if mode == "nufft" else None
