@@ -171,6 +171,16 @@ isam_status isam_max_abs(isam_plan* plan, const void* eta, double* out);
 isam_status isam_max_abs_noalloc(const void* x, int64_t n, int32_t precision, double* out,
                                  void* stream);
 
+/* The filter B(q, k) of Eq. 3 (b of Eq. 16) for the lens and the intensity
+ * drop-off; the paper's results use B = 1 (§3.2), which is the default.
+ * b: host complex table, interleaved (re, im) doubles, [ny/2 + 1][nx/2 + 1][nk]
+ * (one row block when ny = 1); entry (|my|, |mx|, j) multiplies the spectral
+ * sample (q = (±mx, ±my) in FFT index, k_j), so B is symmetric in q.  NULL
+ * restores B = 1.  A, A^H, solves, calibration and batches then use
+ * S = B . e^{j phi} e^{j(2k+beta)z0} . H.  Rebuilds the phase tables, forgets
+ * the cached L; ISAM_ERR_INVALID for non-finite entries.  Synchronous. */
+isam_status isam_set_filter(isam_plan* plan, const double* b);
+
 /* The direct dispersion-compensated reconstruction of Eq. 9 on the full-range
  * depth grid, A-scan by A-scan (the exact adjoint of the ISAM_FLAG_AXIAL_MODEL
  * operator, evaluated as an nz-point FFT):

@@ -37,6 +37,8 @@ template <typename T> struct Tables {
   T* scale = nullptr;        // [nz]  s(n - nz/2) / sqrt(nz)
   cplx<T>* disp = nullptr;   // [nk]  e^{j phi(k_j)}
   StoltEntry<T>* stab = nullptr;  // [(ny/2+1)(nx/2+1)][nk] or null (computed on the fly)
+  cplx<T>* filt = nullptr;   // [(ny/2+1)(nx/2+1)][nk] filter B of Eq. 3, or null (B = 1);
+                             // folded into stab's phases when stab exists
 };
 
 // Min-max coefficients as polynomials in the fractional offset f.  With

@@ -68,6 +68,8 @@ struct isam_plan {
   // and whether the fused kernel reads the Stolt table (1) or evaluates (2)
   int tune_tp = 0;
   int tune_table = 0;
+  // filter B of Eq. 3 per |q| class, interleaved (re, im); empty: B = 1
+  std::vector<double> filt_host;
   double* cpartial = nullptr;   // [npairs][5] calibration partial sums
   int64_t launches = 0;
   size_t n_img = 0, n_spec = 0;
@@ -159,7 +161,7 @@ template <typename T> isam_status dalloc(T** p, size_t n) {
 }
 
 template <typename T> void impl_free(Impl<T>& im) {
-  cudaFree(im.tab.scale); cudaFree(im.tab.disp); cudaFree(im.tab.stab);
+  cudaFree(im.tab.scale); cudaFree(im.tab.disp); cudaFree(im.tab.stab); cudaFree(im.tab.filt);
   cudaFree(im.eta_hat); cudaFree(im.spec); cudaFree(im.grad); cudaFree(im.sdh);
   cudaFree(im.zA); cudaFree(im.zB); cudaFree(im.s_tmp);
   cudaFree(im.s_host_stage); cudaFree(im.out_stage);
@@ -184,6 +186,18 @@ template <typename T> bool precision_fits(const isam_plan* P) {
 // Asynchronous on the plan's stream (the host vector is copied synchronously).
 template <typename T> isam_status phase_tables(isam_plan* P, Impl<T>& im) {
   const isam_params& p = P->p;
+  const size_t rows = size_t(P->ny / 2 + 1) * (P->nx / 2 + 1);
+  // filter B (before the Stolt table, which folds it into its phases)
+  if (P->filt_host.empty()) {
+    cudaFree(im.tab.filt);
+    im.tab.filt = nullptr;
+  } else {
+    std::vector<cplx<T>> h(rows * P->nk);
+    for (size_t i = 0; i < h.size(); ++i)
+      h[i] = mk<T>(T(P->filt_host[2 * i]), T(P->filt_host[2 * i + 1]));
+    if (!im.tab.filt) ISAM_TRY(dalloc(&im.tab.filt, h.size()));
+    CUDA_TRY(cudaMemcpy(im.tab.filt, h.data(), sizeof(cplx<T>) * h.size(), cudaMemcpyHostToDevice));
+  }
   {
     std::vector<cplx<T>> h(P->nk);
     const double dk = (p.k_max - p.k_min) / (P->nk - 1);
@@ -198,7 +212,6 @@ template <typename T> isam_status phase_tables(isam_plan* P, Impl<T>& im) {
     CUDA_TRY(cudaMemcpy(im.tab.disp, h.data(), sizeof(cplx<T>) * P->nk, cudaMemcpyHostToDevice));
   }
   {
-    const size_t rows = size_t(P->ny / 2 + 1) * (P->nx / 2 + 1);
     const size_t bytes = rows * P->nk * sizeof(StoltEntry<T>);
     if (bytes <= kStoltTableMaxBytes && !(p.flags & ISAM_FLAG_NO_STOLT_TABLE)) {
       if (!im.tab.stab) ISAM_TRY(dalloc(&im.tab.stab, rows * P->nk));
@@ -1134,6 +1147,22 @@ isam_status isam_set_model(isam_plan* P, int32_t n_disp, const double* disp, dou
   for (int i = 0; i < 4; ++i) P->p.disp[i] = i < n_disp ? disp[i] : 0.0;
   P->p.z0 = z0;
   make_stolt(P);
+  if (P->f32.ready) ISAM_TRY(phase_tables<float>(P, P->f32));
+  if (P->f64.ready) ISAM_TRY(phase_tables<double>(P, P->f64));
+  P->L_cache = 0.0;
+  return from_cuda(cudaStreamSynchronize(P->stream));
+}
+
+isam_status isam_set_filter(isam_plan* P, const double* b) {
+  if (!P) return ISAM_ERR_INVALID;
+  const size_t n = 2 * size_t(P->ny / 2 + 1) * (P->nx / 2 + 1) * P->nk;
+  if (b)
+    for (size_t i = 0; i < n; ++i)
+      if (!isfinite(b[i])) return ISAM_ERR_INVALID;
+  DeviceGuard g(P->device);
+  CUDA_TRY(cudaStreamSynchronize(P->stream));
+  if (b) P->filt_host.assign(b, b + n);
+  else P->filt_host.clear();
   if (P->f32.ready) ISAM_TRY(phase_tables<float>(P, P->f32));
   if (P->f64.ready) ISAM_TRY(phase_tables<double>(P, P->f64));
   P->L_cache = 0.0;

@@ -108,7 +108,8 @@ __device__ __forceinline__ cplx<T> spectral_phase(const StoltConst& sc, const cp
   return ph;
 }
 
-// Row of the Stolt table for lateral frequency (mx, my) (rows by |mx|, |my|).
+// Row of the Stolt table (and of the filter table) for lateral frequency
+// (mx, my): rows by |mx|, |my|.
 __device__ __forceinline__ int stolt_class(const StoltConst& sc, int mx, int my) {
   return abs(my) * (sc.nx / 2 + 1) + abs(mx);
 }
@@ -118,8 +119,11 @@ __device__ __forceinline__ int stolt_class(const StoltConst& sc, int mx, int my)
 template <typename T> struct Positions {
   StoltPos<T> sp;
   const StoltEntry<T>* row;
+  const cplx<T>* frow;       // filter B of this column's |q| class (evaluated path)
   __device__ Positions(const AxArgs<T>& A, int mx, int my) : sp(A.sc, mx, my) {
-    row = A.tab.stab ? A.tab.stab + size_t(stolt_class(A.sc, mx, my)) * A.sc.nk : nullptr;
+    const size_t cls = size_t(stolt_class(A.sc, mx, my)) * A.sc.nk;
+    row = A.tab.stab ? A.tab.stab + cls : nullptr;
+    frow = A.tab.filt ? A.tab.filt + cls : nullptr;
   }
   __device__ __forceinline__ bool at(const AxArgs<T>& A, int j, int& mfl, T& frac,
                                      cplx<T>& ph) const {
@@ -133,6 +137,7 @@ template <typename T> struct Positions {
     T turn;
     if (!sp.at(A.sc, j, mfl, frac, turn)) return false;
     ph = spectral_phase<T>(A.sc, A.tab.disp, j, turn);
+    if (frow) ph = cmul(ph, __ldg(frow + j));
     return true;
   }
 };
@@ -515,6 +520,7 @@ __global__ void k_stolt_table(const __grid_constant__ AxArgs<T> A, StoltEntry<T>
   T turn;
   if (sp.at(A.sc, j, e.mfl, e.frac, turn)) {
     e.ph = spectral_phase<T>(A.sc, A.tab.disp, j, turn);
+    if (A.tab.filt) e.ph = cmul(e.ph, A.tab.filt[size_t(cls) * A.sc.nk + j]);
   } else {
     e.mfl = INT_MIN;
     e.frac = T(0);

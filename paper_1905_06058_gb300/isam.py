@@ -85,6 +85,7 @@ _SIGS = {
                                      ctypes.POINTER(ctypes.c_int32)]),
     "isam_batch_kernel_count": (ctypes.c_int64, [_P]),
     "isam_batch_destroy": (None, [_P]),
+    "isam_set_filter": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
     "isam_set_model": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                       ctypes.c_double]),
     "isam_param_grad": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
@@ -302,6 +303,21 @@ class Plan:
         d = [float(v) for v in disp]
         arr = (ctypes.c_double * 4)(*(d + [0.0] * (4 - len(d))))
         _check(_lib.isam_set_model(self._h, len(d), arr, float(z0)), "isam_set_model")
+
+    def set_filter(self, table) -> None:
+        """isam_set_filter: complex table [ny//2 + 1, nx//2 + 1, nk] over |q| classes
+        (B of Eq. 3), or None for B = 1."""
+        import numpy as np
+        self._sync_stream()
+        if table is None:
+            _check(_lib.isam_set_filter(self._h, None), "isam_set_filter")
+            return
+        g = self.geom
+        shape = ((g.ny // 2 + 1) if g.ny > 1 else 1, g.nx // 2 + 1, g.nk)
+        t = np.ascontiguousarray(np.broadcast_to(np.asarray(table, np.complex128), shape))
+        buf = t.view(np.float64).ravel()
+        _check(_lib.isam_set_filter(self._h, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+               "isam_set_filter")
 
     def param_grad(self, x, y):
         """isam_param_grad: <dA/dtheta x, y> for theta = (a1..a4, z0), as a float64 array."""
