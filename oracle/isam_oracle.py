@@ -18,6 +18,8 @@ What it computes (paper section / equation in brackets):
     with coefficients that minimise the worst-case error, solved per point;
 * adjoint  A^H y = K_hat^H y under the real inner product  [Eq. 17];
 * weighted complex soft threshold [Eq. 14], relative residual [Eq. 15],
+  the prox of an l1 prior on orthonormal Haar detail coefficients along depth
+  (one of the other convex priors §3.1 names),
   FISTA [Alg. 1], residual add-back [Alg. 1, optional last step];
 * Lipschitz constant of the gradient by power iteration;
 * the optional filter B(q, k) of Eq. 3 (b of Eq. 16), as a table over |q|;
@@ -378,6 +380,45 @@ def soft_threshold(u: np.ndarray, tau) -> np.ndarray:
     return r
 
 
+def haar_forward(x: np.ndarray) -> np.ndarray:
+    """Orthonormal Haar transform along the last axis (length 2^m, all levels).
+
+    Level by level on the current approximation a (length n): a' = (a[0::2] +
+    a[1::2])/sqrt 2, d = (a[0::2] - a[1::2])/sqrt 2; the output is
+    [a_final, d_coarsest, ..., d_finest] (Mallat order)."""
+    a = np.asarray(x, dtype=np.complex128)
+    details = []
+    while a.shape[-1] > 1:
+        e, o = a[..., 0::2], a[..., 1::2]
+        details.append((e - o) / math.sqrt(2))
+        a = (e + o) / math.sqrt(2)
+    return np.concatenate([a] + details[::-1], axis=-1)
+
+
+def haar_inverse(c: np.ndarray) -> np.ndarray:
+    """Inverse of haar_forward."""
+    c = np.asarray(c, dtype=np.complex128)
+    n = c.shape[-1]
+    a = c[..., :1]
+    pos = 1
+    while pos < n:
+        d = c[..., pos:2 * pos]
+        out = np.empty(c.shape[:-1] + (2 * pos,), np.complex128)
+        out[..., 0::2] = (a + d) / math.sqrt(2)
+        out[..., 1::2] = (a - d) / math.sqrt(2)
+        a = out
+        pos *= 2
+    return a
+
+
+def haar_prox(u: np.ndarray, tau) -> np.ndarray:
+    """prox of tau * (l1 norm of the Haar detail coefficients along depth):
+    W^H T_tau(W u) with the approximation coefficient kept (W orthonormal)."""
+    c = haar_forward(u)
+    c[..., 1:] = soft_threshold(c[..., 1:], tau)
+    return haar_inverse(c)
+
+
 def relative_residual(z, eta, g, eps=1e-12) -> float:
     """r_r = ||z - eta|| / (max(||g||, ||z - eta + g||) + eps)  [Eq. 15]."""
     d = z - eta
@@ -428,11 +469,13 @@ class FistaResult:
 
 def fista(A: Callable, AH: Callable, s_d: np.ndarray, lam: float, L: float, w=1.0,
           max_iter: int = 100, tol: float = 0.0, eps: float = 1e-12,
-          addback: bool = False, shape=None) -> FistaResult:
+          addback: bool = False, shape=None, prox: Optional[Callable] = None) -> FistaResult:
     """MBIR full-range ISAM, Alg. 1, with step 1/L and threshold lambda w / L.
 
     Each iteration: g = (1/L) A^H(A eta - s_d); z = T(eta - g); stop when the
-    relative residual (Eq. 15) drops below ``tol``; momentum update.
+    relative residual (Eq. 15) drops below ``tol``; momentum update.  ``prox``
+    (optional) replaces T for another convex prior (§3.1): z = prox(eta - g,
+    lambda / L).
     """
     eta = np.zeros(shape, np.complex128)
     z_prev = np.zeros(shape, np.complex128)
@@ -442,7 +485,7 @@ def fista(A: Callable, AH: Callable, s_d: np.ndarray, lam: float, L: float, w=1.
     z = z_prev
     for k in range(1, max_iter + 1):
         g = AH(A(eta) - s_d) / L
-        z = soft_threshold(eta - g, lam * w / L)
+        z = soft_threshold(eta - g, lam * w / L) if prox is None else prox(eta - g, lam / L)
         rr = relative_residual(z, eta, g, eps)
         if rr < tol:
             break
