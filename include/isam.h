@@ -99,7 +99,17 @@ typedef struct {
   int32_t residual_addback; /* 1: return z + (1/L) A^H (s_d - A z) (Alg. 1 end)   */
   double L;                 /* step 1/L; 0: power-iteration estimate, cached      */
   double eps;               /* r_r denominator guard (0: 1e-30)                   */
+  int32_t prior;            /* ISAM_PRIOR_* (0: the weighted l1 of Eq. 12)         */
 } isam_solve_opts;
+
+/* Priors of the MBIR objective (§3.1: Eq. 12 extends to other convex priors):
+ * ISAM_PRIOR_L1: lambda w^T |eta| (Eq. 12), prox = the soft threshold of Eq. 14.
+ * ISAM_PRIOR_HAAR_DEPTH: lambda ||details(W eta)||_1, W the orthonormal Haar
+ *   transform along depth of every A-scan (all log2(nz) levels, the coarsest
+ *   approximation coefficient unpenalised); prox = W^H T_{lambda/L}(W u).
+ *   Needs w_dev = NULL and tol = 0 (ISAM_ERR_UNSUPPORTED otherwise); not
+ *   available to the unrolled (calibration) entry points. */
+enum { ISAM_PRIOR_L1 = 0, ISAM_PRIOR_HAAR_DEPTH = 1 };
 
 /* Resumable solver state (checkpoint/restart).  z1 = z^{k}, z2 = z^{k-1} are
  * caller-owned device images; k iterations are done.  Pass k = 0 to start. */

@@ -63,6 +63,8 @@ enum LatMode : int {
   LAT_R2C_FWD = 2,   // real input, X = F x
   LAT_INV_REAL = 3,  // real output, Re(F^-1 x)
   LAT_UPDATE = 5,    // FISTA step in image space between F^-1 and F
+  LAT_GRAD_STEP = 6, // u = eta^k - g/L after F^-1 (no threshold, no F): other priors
+  LAT_EXTRAP_FWD = 7,// X = F(z1 + mu (z1 - z2)): the momentum step, then F
 };
 
 template <typename T> struct LatArgs {
@@ -155,6 +157,12 @@ template <typename T> cudaError_t launch_st_vjp(const cplx<T>* u, const cplx<T>*
 template <typename T> cudaError_t launch_bwd_combine(const cplx<T>* ubar, const cplx<T>* b,
                                                      T inv_L, T mu, cplx<T>* zb1, cplx<T>* zb2,
                                                      size_t n, cudaStream_t s);
+
+// prox of tau ||details(W u)||_1, W the orthonormal Haar transform along depth
+// of each A-scan (k_lateral.cu); tau = lam_scale * (*lam_dev) when lam_dev
+template <typename T> cudaError_t launch_haar_prox(const cplx<T>* u, cplx<T>* z, int nz,
+                                                   size_t n_ascans, T tau, const double* lam_dev,
+                                                   double lam_scale, cudaStream_t s);
 
 // Eq. 9 direct reconstruction (k_direct.cu)
 template <typename T> cudaError_t launch_dc_ifft(const T* s, cplx<T>* out, const cplx<T>* disp,

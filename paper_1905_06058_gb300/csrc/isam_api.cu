@@ -394,13 +394,37 @@ template <typename T> isam_status fista_iteration(isam_plan* P, Impl<T>& im,
                                                   cplx<T>* ehat_out = nullptr,
                                                   cplx<T>* u_out = nullptr,
                                                   const double* lam_dev = nullptr,
-                                                  double lam_scale = 0.0) {
+                                                  double lam_scale = 0.0,
+                                                  int prior = ISAM_PRIOR_L1) {
   cudaStream_t s = P->stream;
   if (!ehat_in) ehat_in = im.eta_hat;
   if (!ehat_out) ehat_out = im.eta_hat;
   AxArgs<T> ax = ax_args<T>(P, im, ehat_in, im.grad);
   ax.sdh = im.sdh;
   ISAM_TRY(launch(P, ISAM_KCLASS_AX_FUSED, [&] { return launch_ax_fused<T>(ax, P->npairs, s); }));
+  if (prior == ISAM_PRIOR_HAAR_DEPTH) {
+    // u^k = eta^k - g/L in image space (in place over G_hat), the Haar prox to
+    // z^k, then eta_hat^{k+1} = F(z^k + mu_k (z^k - z^{k-1}))
+    LatArgs<T> g;
+    if (P->ny == 1) {
+      g = lat_args<T>(1, P->nx, P->nz, im.grad, im.grad);
+    } else {
+      ISAM_TRY(lat<T>(P, LAT_C2C_INV, lat_args<T>(P->ny, P->nx, P->nz, im.grad, im.grad)));
+      g = lat_args<T>(1, P->ny, P->nx * P->nz, im.grad, im.grad);
+    }
+    g.z1 = z1; g.z2 = z2; g.inv_L = T(1.0 / L); g.mu_prev = T(mu_prev); g.flag = P->flag;
+    ISAM_TRY(lat<T>(P, LAT_GRAD_STEP, g));
+    ISAM_TRY(launch(P, ISAM_KCLASS_MISC, [&] {
+      return launch_haar_prox<T>(im.grad, zout, P->nz, size_t(P->nx) * P->ny, T(lam / L), lam_dev,
+                                 lam_scale, s);
+    }));
+    LatArgs<T> e = lat_args<T>(P->ny, P->nx, P->nz, nullptr, ehat_out);
+    e.z1 = zout; e.z2 = z1; e.mu = T(mu);
+    ISAM_TRY(lat<T>(P, LAT_EXTRAP_FWD, e));
+    if (P->ny > 1)
+      ISAM_TRY(lat<T>(P, LAT_C2C_FWD, lat_args<T>(1, P->ny, P->nx * P->nz, ehat_out, ehat_out)));
+    return ISAM_OK;
+  }
   LatArgs<T> u;
   if (P->ny == 1) {
     u = lat_args<T>(1, P->nx, P->nz, im.grad, ehat_out);
@@ -498,7 +522,8 @@ template <typename T> isam_status solve_impl(isam_plan* P, const T* s_d, const i
     const int k = k0 + it;
     const bool norms = check && (it % every == 0 || it == o->max_iter);
     ISAM_TRY(fista_iteration<T>(P, im, zP, zQ, zQ, static_cast<const T*>(o->w_dev), lam, L,
-                                mu[k - 1], mu[k], norms));
+                                mu[k - 1], mu[k], norms, nullptr, nullptr, nullptr, nullptr, 0.0,
+                                o->prior));
     std::swap(zP, zQ);   // zP = z^k, zQ = z^{k-1}
     done = it;
     if (norms) {
@@ -812,6 +837,8 @@ static isam_status check_opts(const isam_plan* P, const isam_solve_opts* o) {
   if (o->max_iter < 1) return ISAM_ERR_INVALID;
   if (!(o->lambda_abs > 0) && !(o->lambda_rel >= 0)) return ISAM_ERR_INVALID;
   if (o->tol < 0 || !isfinite(o->tol)) return ISAM_ERR_INVALID;
+  if (o->prior != ISAM_PRIOR_L1 && o->prior != ISAM_PRIOR_HAAR_DEPTH) return ISAM_ERR_INVALID;
+  if (o->prior == ISAM_PRIOR_HAAR_DEPTH && (o->w_dev || o->tol > 0)) return ISAM_ERR_UNSUPPORTED;
   (void)P;
   return ISAM_OK;
 }
@@ -990,6 +1017,7 @@ isam_status check_unrolled_opts(const isam_plan* P, const isam_solve_opts* o, in
   if (!(o->lambda_abs > 0) || !(o->L > 0) || !isfinite(o->lambda_abs) || !isfinite(o->L))
     return ISAM_ERR_INVALID;
   if (o->residual_addback) return ISAM_ERR_INVALID;
+  if (o->prior != ISAM_PRIOR_L1) return ISAM_ERR_UNSUPPORTED;
   (void)P;
   return ISAM_OK;
 }
@@ -1338,7 +1366,7 @@ template <typename T> isam_status batch_enqueue(isam_plan* P, const T* s_d,
   const T* w = static_cast<const T*>(o->w_dev);
   for (int k = 1; k <= o->max_iter; ++k) {
     ISAM_TRY(fista_iteration<T>(P, im, zP, zQ, zQ, w, lam, L, mu[k - 1], mu[k], false, nullptr,
-                                nullptr, nullptr, lam_dev, lam_scale));
+                                nullptr, nullptr, lam_dev, lam_scale, o->prior));
     std::swap(zP, zQ);
   }
   if (o->residual_addback) {

@@ -97,6 +97,10 @@ __global__ void __launch_bounds__(512, 2) k_lat(const __grid_constant__ LatArgs<
         const RP r = *reinterpret_cast<const RP*>(static_cast<const T*>(a.in) + gi);
         v[i].a = mk<T>(r.x, T(0));
         v[i].b = mk<T>(r.y, T(0));
+      } else if (MODE == LAT_EXTRAP_FWD) {
+        const V z1 = *reinterpret_cast<const V*>(a.z1 + gi);
+        const V z2 = *reinterpret_cast<const V*>(a.z2 + gi);
+        v[i] = eadd(z1, escale(esub(z1, z2), a.mu));
       } else {
         v[i] = *reinterpret_cast<const V*>(static_cast<const C*>(a.in) + gi);
       }
@@ -109,13 +113,14 @@ __global__ void __launch_bounds__(512, 2) k_lat(const __grid_constant__ LatArgs<
   }
   __syncthreads();
 
-  if (MODE == LAT_C2C_FWD || MODE == LAT_R2C_FWD)
+  if (MODE == LAT_C2C_FWD || MODE == LAT_R2C_FWD || MODE == LAT_EXTRAP_FWD)
     fft_smem<-1, false, T>(buf, TP, col, b, L, a.logL, tw, true, a.r3);
   else
     fft_smem<+1, false, T>(buf, TP, col, b, L, a.logL, tw, true, a.r3);
 
   const T nrm = a.norm;
-  if (MODE == LAT_C2C_FWD || MODE == LAT_C2C_INV || MODE == LAT_R2C_FWD) {
+  if (MODE == LAT_C2C_FWD || MODE == LAT_C2C_INV || MODE == LAT_R2C_FWD ||
+      MODE == LAT_EXTRAP_FWD) {
     C* out = static_cast<C*>(a.out);
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
@@ -137,6 +142,26 @@ __global__ void __launch_bounds__(512, 2) k_lat(const __grid_constant__ LatArgs<
       r.y = v.b.x * nrm;
       *reinterpret_cast<RP*>(out + gidx(e)) = r;
     }
+    return;
+  }
+  if (MODE == LAT_GRAD_STEP) {
+    // u = eta^k - g/L with eta^k = z1 + mu_prev (z1 - z2), written to out
+    const T sg = nrm * a.inv_L;
+    C* out = static_cast<C*>(a.out);
+    bool bad = false;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      if (i >= ept) break;
+      const int e = tid + i * nt;
+      const size_t gi = gidx(e);
+      const V z1 = *reinterpret_cast<const V*>(a.z1 + gi);
+      const V z2 = *reinterpret_cast<const V*>(a.z2 + gi);
+      const V eta = eadd(z1, escale(esub(z1, z2), a.mu_prev));
+      const V u = esub(eta, escale(buf[sidx(e)], sg));
+      *reinterpret_cast<V*>(out + gi) = u;
+      bad |= !(isfinite(u.a.x) && isfinite(u.a.y) && isfinite(u.b.x) && isfinite(u.b.y));
+    }
+    if (bad) atomicOr(a.flag, 1);
     return;
   }
   // LAT_UPDATE, in two batches of four elements: loads of the iterates first
@@ -217,6 +242,61 @@ __global__ void __launch_bounds__(512, 2) k_lat(const __grid_constant__ LatArgs<
   }
 }
 
+// prox of tau ||details(W u)||_1 per A-scan (nz contiguous samples), W the
+// orthonormal Haar transform along depth: in-place lifting levels with
+// stride h = 1, 2, .., nz/2 (pair (i, i + h), i a multiple of 2h, becomes
+// ((x_i + x_{i+h})/sqrt 2, (x_i - x_{i+h})/sqrt 2)), the complex soft
+// threshold on every coefficient but the approximation (index 0), and the
+// same butterflies in reverse order, which invert them.
+template <typename T>
+__global__ void k_haar_prox(const cplx<T>* u, cplx<T>* z, int nz, T tau, const double* lam_dev,
+                            double lam_scale) {
+  extern __shared__ __align__(16) unsigned char raw[];
+  cplx<T>* x = reinterpret_cast<cplx<T>*>(raw);
+  const size_t col = blockIdx.x;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < nz; i += nt) x[i] = u[col * nz + i];
+  __syncthreads();
+  const T r = T(0.70710678118654752440);
+  for (int h = 1; h < nz; h <<= 1) {
+    for (int p = tid; p < nz / (2 * h); p += nt) {
+      const int i = p * 2 * h;
+      const cplx<T> a0 = x[i], a1 = x[i + h];
+      x[i] = cscale(cadd(a0, a1), r);
+      x[i + h] = cscale(csub(a0, a1), r);
+    }
+    __syncthreads();
+  }
+  const T t = lam_dev ? T(lam_scale * *lam_dev) : tau;
+  for (int i = tid; i < nz; i += nt)
+    if (i) x[i] = soft_threshold(x[i], t);
+  __syncthreads();
+  for (int h = nz >> 1; h >= 1; h >>= 1) {
+    for (int p = tid; p < nz / (2 * h); p += nt) {
+      const int i = p * 2 * h;
+      const cplx<T> a0 = x[i], a1 = x[i + h];
+      x[i] = cscale(cadd(a0, a1), r);
+      x[i + h] = cscale(csub(a0, a1), r);
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < nz; i += nt) z[col * nz + i] = x[i];
+}
+
+template <typename T> cudaError_t launch_haar_prox(const cplx<T>* u, cplx<T>* z, int nz,
+                                                   size_t n_ascans, T tau, const double* lam_dev,
+                                                   double lam_scale, cudaStream_t s) {
+  const int threads = nz / 2 >= 256 ? 256 : (nz / 2 >= 32 ? nz / 2 : 32);
+  const size_t sm = size_t(nz) * sizeof(cplx<T>);
+  cudaFuncSetAttribute(k_haar_prox<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+  k_haar_prox<T><<<unsigned(n_ascans), threads, sm, s>>>(u, z, nz, tau, lam_dev, lam_scale);
+  return cudaGetLastError();
+}
+template cudaError_t launch_haar_prox<float>(const float2*, float2*, int, size_t, float,
+                                             const double*, double, cudaStream_t);
+template cudaError_t launch_haar_prox<double>(const double2*, double2*, int, size_t, double,
+                                              const double*, double, cudaStream_t);
+
 template <typename T> size_t lat_smem_bytes(int L, int TP) {
   int lg = 0, r3 = 0;
   fft_length(L, &lg, &r3);
@@ -241,6 +321,8 @@ template <typename T> cudaError_t launch_lat(int mode, const LatArgs<T>& a, cuda
     case LAT_R2C_FWD: return launch_lat_mode<T, LAT_R2C_FWD>(a, s);
     case LAT_INV_REAL: return launch_lat_mode<T, LAT_INV_REAL>(a, s);
     case LAT_UPDATE: return launch_lat_mode<T, LAT_UPDATE>(a, s);
+    case LAT_GRAD_STEP: return launch_lat_mode<T, LAT_GRAD_STEP>(a, s);
+    case LAT_EXTRAP_FWD: return launch_lat_mode<T, LAT_EXTRAP_FWD>(a, s);
   }
   return cudaErrorInvalidValue;
 }

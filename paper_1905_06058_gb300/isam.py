@@ -44,7 +44,10 @@ class SolveOpts(ctypes.Structure):
                 ("max_iter", ctypes.c_int32), ("tol", ctypes.c_double),
                 ("check_every", ctypes.c_int32), ("w_dev", ctypes.c_void_p),
                 ("residual_addback", ctypes.c_int32), ("L", ctypes.c_double),
-                ("eps", ctypes.c_double)]
+                ("eps", ctypes.c_double), ("prior", ctypes.c_int32)]
+
+
+PRIORS = {"l1": 0, "haar_depth": 1}
 
 
 class SolveState(ctypes.Structure):
@@ -231,8 +234,10 @@ class Plan:
             "isam_dispersion_compensated_ifft")
         return out
 
-    def _opts(self, lambda_rel, lambda_abs, max_iter, tol, check_every, w, addback, L, eps):
+    def _opts(self, lambda_rel, lambda_abs, max_iter, tol, check_every, w, addback, L, eps,
+              prior="l1"):
         o = SolveOpts()
+        o.prior = PRIORS[prior]
         o.lambda_rel, o.lambda_abs = float(lambda_rel), float(lambda_abs)
         o.max_iter, o.tol, o.check_every = int(max_iter), float(tol), int(check_every)
         o.w_dev = None if w is None else self._dev(w, self.real_dtype, (self.image_shape[2],), "w")
@@ -241,7 +246,8 @@ class Plan:
         return o
 
     def solve(self, s, lambda_rel=0.01, lambda_abs=0.0, max_iter=100, tol=0.0, check_every=10,
-              w=None, addback=False, L=0.0, eps=0.0, out=None, state: Optional[dict] = None):
+              w=None, addback=False, L=0.0, eps=0.0, out=None, state: Optional[dict] = None,
+              prior: str = "l1"):
         """MBIR solve (Alg. 1).  Returns (eta, info dict).  ``state`` (optional) is a dict
         with CUDA tensors 'z1', 'z2' (images) and ints/floats 'k', 'lambda', 'L'; it is
         updated in place for checkpoint / resume."""
@@ -249,7 +255,8 @@ class Plan:
         self._sync_stream()
         if out is None:
             out = torch.empty(self.image_shape, dtype=self.cplx_dtype, device=s.device)
-        o = self._opts(lambda_rel, lambda_abs, max_iter, tol, check_every, w, addback, L, eps)
+        o = self._opts(lambda_rel, lambda_abs, max_iter, tol, check_every, w, addback, L, eps,
+                       prior)
         info = SolveInfo()
         st_ptr = None
         if state is not None:
@@ -421,7 +428,8 @@ class Batch:
             outs[i] = plan._dev(out, plan.cplx_dtype, plan.image_shape, "out")
             opts[i] = plan._opts(kw.get("lambda_rel", 0.01), kw.get("lambda_abs", 0.0),
                                  kw.get("max_iter", 100), 0.0, 1, kw.get("w"),
-                                 kw.get("addback", False), kw.get("L", 0.0), 0.0)
+                                 kw.get("addback", False), kw.get("L", 0.0), 0.0,
+                                 kw.get("prior", "l1"))
             self._keep.append((plan, s, out, kw.get("w")))
         self.n = n
         h = _P()

@@ -55,7 +55,7 @@ int main(void) {
   P(isam_params, disp) P(isam_params, precision) P(isam_params, nufft_os)
   P(isam_params, flags)
   P(isam_solve_opts, max_iter) P(isam_solve_opts, w_dev) P(isam_solve_opts, L)
-  P(isam_solve_opts, eps) P(isam_solve_state, k) P(isam_solve_state, L)
+  P(isam_solve_opts, eps) P(isam_solve_opts, prior) P(isam_solve_state, k) P(isam_solve_state, L)
   P(isam_solve_info, rr) P(isam_solve_info, status)
   return 0;
 }
