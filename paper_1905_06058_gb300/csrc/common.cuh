@@ -72,11 +72,6 @@ __device__ __forceinline__ ff ff_mul_f(ff a, float b) {
   p.lo = __fmaf_rn(a.lo, b, p.lo);
   return ff_quick(p.hi, p.lo);
 }
-__device__ __forceinline__ ff ff_sqrt(ff a) {  // a > 0
-  float r = __fsqrt_rn(a.hi);
-  float e = __fadd_rn(__fmaf_rn(-r, r, a.hi), a.lo);
-  return ff_quick(r, __fdiv_rn(e, __fmul_rn(2.0f, r)));
-}
 // float-float square root from an approximate seed r ~ sqrt(a.hi) (a few ulp):
 // one Newton correction d = (a - r^2) / (2r), with r^2 formed exactly by an FMA
 // and the division by an approximate reciprocal, gives ~44 significant bits.
@@ -84,15 +79,6 @@ __device__ __forceinline__ ff ff_sqrt_fast(ff a) {  // a > 0
   const float r = a.hi * rsqrtf(a.hi);
   const float e = __fadd_rn(__fmaf_rn(-r, r, a.hi), a.lo);
   return ff_quick(r, __fdividef(e, 2.0f * r));
-}
-__device__ __forceinline__ ff ff_div(ff a, ff b) {
-  float q1 = __fdiv_rn(a.hi, b.hi);
-  ff r = ff_sub(a, ff_mul_f(b, q1));
-  float q2 = __fdiv_rn(r.hi, b.hi);
-  r = ff_sub(r, ff_mul_f(b, q2));
-  float q3 = __fdiv_rn(r.hi, b.hi);
-  ff q = ff_quick(q1, q2);
-  return ff_add(q, {q3, 0.0f});
 }
 
 }  // namespace isam

@@ -161,22 +161,6 @@ __device__ __forceinline__ void coefficients(const Poly<T>& P, T frac, T* c) {
   }
 }
 
-// one coefficient c_l(f)
-template <typename T, int J>
-__device__ __forceinline__ T coefficient(const Poly<T>& P, T frac, int l) {
-  constexpr int DE = PolyDeg<T>::DE, DO = PolyDeg<T>::DO;
-  const T x = frac - T(0.5);
-  const T y = T(4) * x * x;
-  const int p = l < J / 2 ? l : J - 1 - l;
-  T e = P.e[p][DE];
-#pragma unroll
-  for (int k = DE - 1; k >= 0; --k) e = fma(e, y, P.e[p][k]);
-  T o = P.o[p][DO];
-#pragma unroll
-  for (int k = DO - 1; k >= 0; --k) o = fma(o, y, P.o[p][k]);
-  return fma(l < J / 2 ? x : -x, o, e);
-}
-
 template <typename T>
 __device__ __forceinline__ void pair_columns(const AxArgs<T>& A, int& c1, int& c2, int& mx,
                                              int& my) {
