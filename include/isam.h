@@ -39,6 +39,7 @@
 #ifndef ISAM_H
 #define ISAM_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -100,6 +101,7 @@ typedef struct {
   double L;                 /* step 1/L; 0: power-iteration estimate, cached      */
   double eps;               /* r_r denominator guard (0: 1e-30)                   */
   int32_t prior;            /* ISAM_PRIOR_* (0: the weighted l1 of Eq. 12)         */
+  int32_t objective;        /* 1: report the Eq. 12 objective of z^K in the info   */
 } isam_solve_opts;
 
 /* Priors of the MBIR objective (§3.1: Eq. 12 extends to other convex priors):
@@ -127,7 +129,22 @@ typedef struct {
   double lambda;       /* regularisation used                                 */
   double L;            /* Lipschitz constant used                             */
   int32_t status;      /* isam_status of the solve                            */
+  double objective;    /* 1/2 ||A z^K - s_d||^2 + lambda w^T |z^K| (Eq. 12) when
+                          asked for with the l1 prior, else -1; z^K before any
+                          add-back; one extra A and two reductions            */
 } isam_solve_info;
+
+/* Device memory of plans (workspace and tables) comes from cudaMalloc unless
+ * an allocator is installed: alloc(bytes, ctx) returns device memory of the
+ * current device or NULL (reported as ISAM_ERR_OOM, and the partly built plan
+ * is released); free(ptr, ctx) returns it.  Process-wide; each block is given
+ * back to the allocator that made it, even after another one is installed.
+ * Both NULL restores cudaMalloc; exactly one NULL is ISAM_ERR_INVALID.  For
+ * pooling allocators of a host framework, and for injecting allocation
+ * failures in tests.  Pinned host staging memory is not affected. */
+typedef void* (*isam_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*isam_free_fn)(void* ptr, void* ctx);
+isam_status isam_set_allocator(isam_alloc_fn alloc, isam_free_fn free_fn, void* ctx);
 
 /* Create a plan: validates p, builds the NUFFT tables (FP64 on the device),
  * allocates workspace on the current device, binds `stream` (a cudaStream_t,
@@ -278,7 +295,10 @@ void isam_batch_destroy(isam_batch* batch);
  * on-the-fly Stolt positions.  Neither choice changes any column's arithmetic.
  * The fastest is kept in the plan and used by later calls; *tile and
  * *stolt_table (nullable) receive it.  Overwrites the plan's workspace.
- * Synchronous. */
+ * When the environment variable ISAM_AUTOTUNE_CACHE names a file, a choice
+ * recorded there for the same device, sizes, precision, J and table mode is
+ * used without timing (if still feasible), and new choices are appended as
+ * lines "<key> -> tile=<t> stolt=<m>".  Synchronous. */
 isam_status isam_autotune(isam_plan* plan, int32_t* tile, int32_t* stolt_table);
 
 /* Kernel launches issued by the last isam_forward / isam_adjoint / isam_solve. */

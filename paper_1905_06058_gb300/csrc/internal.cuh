@@ -124,6 +124,9 @@ template <typename T> cudaError_t launch_max_abs(const cplx<T>* x, size_t n, dou
 template <typename T> cudaError_t launch_norm2(const cplx<T>* x, size_t n, double* partial,
                                                 int nblocks, double* out, cudaStream_t s);
 cudaError_t launch_sum3(const double* partial, int n, double* out, cudaStream_t s);
+template <typename T> cudaError_t launch_wl1(const cplx<T>* x, size_t n, const T* w, int nz,
+                                             double* partial, int nblocks, double* out,
+                                             cudaStream_t s);
 template <typename T> cudaError_t launch_scale(cplx<T>* x, size_t n, const double* denom,
                                                 cudaStream_t s);
 template <typename T> cudaError_t launch_extrapolate(const cplx<T>* z1, const cplx<T>* z2, T mu,

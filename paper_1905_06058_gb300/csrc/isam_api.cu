@@ -9,11 +9,16 @@
 //   adjoint NUFFT) -> LAT_UPDATE (lateral IFFT, FISTA step, lateral FFT).
 // Volumes (ny > 1) add separate x passes around the y-axis update pass.
 #include <math.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
+#include <string>
+
 #include <algorithm>
+#include <mutex>
 #include <new>
+#include <unordered_map>
 #include <vector>
 
 #include "isam.h"
@@ -154,18 +159,65 @@ template <typename F> isam_status launch(isam_plan* P, int cls, F&& f) {
 bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 int ilog2(int v) { int r = 0; while ((1 << r) < v) ++r; return r; }
 
-template <typename T> isam_status dalloc(T** p, size_t n) {
+// Device memory of plans: cudaMalloc, or the allocator installed with
+// isam_set_allocator.  Every block from an installed allocator is recorded
+// with the free function that owns it, so it is returned to that allocator
+// even after another one has been installed.
+struct AllocHook {
+  isam_alloc_fn alloc = nullptr;
+  isam_free_fn free = nullptr;
+  void* ctx = nullptr;
+};
+std::mutex g_alloc_mu;
+AllocHook g_alloc;
+std::unordered_map<void*, AllocHook>& alloc_owners() {
+  static std::unordered_map<void*, AllocHook> m;
+  return m;
+}
+
+isam_status dalloc_bytes(void** p, size_t bytes) {
   *p = nullptr;
-  if (n == 0) return ISAM_OK;
-  return from_cuda(cudaMalloc(reinterpret_cast<void**>(p), n * sizeof(T)));
+  if (bytes == 0) return ISAM_OK;
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  if (g_alloc.alloc) {
+    *p = g_alloc.alloc(bytes, g_alloc.ctx);
+    if (!*p) return ISAM_ERR_OOM;
+    alloc_owners()[*p] = g_alloc;
+    return ISAM_OK;
+  }
+  return from_cuda(cudaMalloc(p, bytes));
+}
+
+void dfree(void* p) {
+  if (!p) return;
+  AllocHook h;
+  bool hooked = false;
+  {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    auto it = alloc_owners().find(p);
+    if (it != alloc_owners().end()) {
+      h = it->second;
+      hooked = true;
+      alloc_owners().erase(it);
+    }
+  }
+  if (hooked) h.free(p, h.ctx);
+  else cudaFree(p);
+}
+
+template <typename T> isam_status dalloc(T** p, size_t n) {
+  void* v = nullptr;
+  const isam_status st = dalloc_bytes(&v, n * sizeof(T));
+  *p = static_cast<T*>(v);
+  return st;
 }
 
 template <typename T> void impl_free(Impl<T>& im) {
-  cudaFree(im.tab.scale); cudaFree(im.tab.disp); cudaFree(im.tab.stab); cudaFree(im.tab.filt);
-  cudaFree(im.eta_hat); cudaFree(im.spec); cudaFree(im.grad); cudaFree(im.sdh);
-  cudaFree(im.zA); cudaFree(im.zB); cudaFree(im.s_tmp);
-  cudaFree(im.s_host_stage); cudaFree(im.out_stage);
-  cudaFree(im.spec2); cudaFree(im.seg); cudaFree(im.cal); cudaFree(im.dc_post);
+  dfree(im.tab.scale); dfree(im.tab.disp); dfree(im.tab.stab); dfree(im.tab.filt);
+  dfree(im.eta_hat); dfree(im.spec); dfree(im.grad); dfree(im.sdh);
+  dfree(im.zA); dfree(im.zB); dfree(im.s_tmp);
+  dfree(im.s_host_stage); dfree(im.out_stage);
+  dfree(im.spec2); dfree(im.seg); dfree(im.cal); dfree(im.dc_post);
   im = Impl<T>();
 }
 
@@ -189,7 +241,7 @@ template <typename T> isam_status phase_tables(isam_plan* P, Impl<T>& im) {
   const size_t rows = size_t(P->ny / 2 + 1) * (P->nx / 2 + 1);
   // filter B (before the Stolt table, which folds it into its phases)
   if (P->filt_host.empty()) {
-    cudaFree(im.tab.filt);
+    dfree(im.tab.filt);
     im.tab.filt = nullptr;
   } else {
     std::vector<cplx<T>> h(rows * P->nk);
@@ -536,6 +588,29 @@ template <typename T> isam_status solve_impl(isam_plan* P, const T* s_d, const i
       if (rr < o->tol) break;
     }
   }
+  // objective of Eq. 12 at z^K
+  double objective = -1.0;
+  if (o->objective && o->prior == ISAM_PRIOR_L1) {
+    if (!im.s_tmp) ISAM_TRY(dalloc(&im.s_tmp, P->n_spec));
+    ISAM_TRY(op_forward<T>(P, zP, im.s_tmp));
+    ISAM_TRY(launch(P, ISAM_KCLASS_MISC, [&] {
+      return launch_rsub<T>(im.s_tmp, s_d, im.s_tmp, P->n_spec, s);
+    }));
+    P->launches += 2;
+    ISAM_TRY(launch(P, ISAM_KCLASS_MISC, [&] {
+      return launch_norm2<T>(reinterpret_cast<const cplx<T>*>(im.s_tmp), P->n_spec / 2,
+                             P->partial, RED_BLOCKS, P->dscal + 5, s);
+    }));
+    ISAM_TRY(launch(P, ISAM_KCLASS_MISC, [&] {
+      return launch_wl1<T>(zP, P->n_img, static_cast<const T*>(o->w_dev), P->nz, P->partial,
+                           RED_BLOCKS, P->dscal + 6, s);
+    }));
+    CUDA_TRY(cudaMemcpyAsync(P->hscal + 5, P->dscal + 5, 2 * sizeof(double),
+                             cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    harvest_events(P);
+    objective = 0.5 * P->hscal[5] * P->hscal[5] + lam * P->hscal[6];
+  }
   // result: z^K, optionally with the residual added back (Alg. 1, last step)
   if (o->residual_addback) {
     if (!im.s_tmp) ISAM_TRY(dalloc(&im.s_tmp, P->n_spec));
@@ -569,6 +644,7 @@ template <typename T> isam_status solve_impl(isam_plan* P, const T* s_d, const i
     info->lambda = lam;
     info->L = L;
     info->status = st;
+    info->objective = objective;
   }
   (void)launches0;
   return st;
@@ -686,8 +762,8 @@ isam_status build_poly(isam_plan* P) {
   if (st == ISAM_OK) st = from_cuda(cudaStreamSynchronize(P->stream));
   if (st == ISAM_OK)
     st = from_cuda(cudaMemcpy(c.data(), dc, sizeof(double) * M * J, cudaMemcpyDeviceToHost));
-  cudaFree(df);
-  cudaFree(dc);
+  dfree(df);
+  dfree(dc);
   if (st != ISAM_OK) return st;
   for (int p = 0; p < J / 2; ++p) {
     std::vector<double> e(M), o(M);
@@ -736,6 +812,15 @@ struct DeviceGuard {
 }  // namespace
 
 extern "C" {
+
+isam_status isam_set_allocator(isam_alloc_fn alloc, isam_free_fn free_fn, void* ctx) {
+  if ((alloc == nullptr) != (free_fn == nullptr)) return ISAM_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  g_alloc.alloc = alloc;
+  g_alloc.free = free_fn;
+  g_alloc.ctx = ctx;
+  return ISAM_OK;
+}
 
 const char* isam_status_string(isam_status s) {
   switch (s) {
@@ -799,11 +884,11 @@ void isam_plan_destroy(isam_plan* P) {
   else cudaDeviceSynchronize();
   impl_free(P->f32);
   impl_free(P->f64);
-  cudaFree(P->partial);
-  cudaFree(P->cpartial);
-  cudaFree(P->pairs);
-  cudaFree(P->dscal);
-  cudaFree(P->flag);
+  dfree(P->partial);
+  dfree(P->cpartial);
+  dfree(P->pairs);
+  dfree(P->dscal);
+  dfree(P->flag);
   if (P->hscal) cudaFreeHost(P->hscal);
   harvest_events(P);
   for (cudaEvent_t e : P->ev_pool) cudaEventDestroy(e);
@@ -951,7 +1036,7 @@ template <typename T> isam_status calib_buffers(isam_plan* P, Impl<T>& im, int s
   if (!im.cal) ISAM_TRY(dalloc(&im.cal, 5 * P->n_img));
   if (!P->cpartial) ISAM_TRY(dalloc(&P->cpartial, size_t(P->npairs) * 5));
   if (seg_cap > im.seg_cap) {
-    cudaFree(im.seg);
+    dfree(im.seg);
     im.seg = nullptr;
     im.seg_cap = 0;
     ISAM_TRY(dalloc(&im.seg, size_t(2 * seg_cap + 1) * P->n_img));
@@ -1504,6 +1589,7 @@ isam_status isam_batch_run(isam_batch* B, isam_solve_info* info) {
       info[i].lambda = lam;
       info[i].L = B->L[i];
       info[i].status = st;
+      info[i].objective = -1.0;
     }
   }
   return first;
@@ -1552,8 +1638,70 @@ template <typename T> isam_status time_iterations(isam_plan* P, int reps, float*
   return st;
 }
 
+// Key of a plan's launch-shape choice in the autotune cache file: the device
+// and everything the timed kernels' shapes depend on.
+std::string tune_key(const isam_plan* P, bool has_table) {
+  cudaDeviceProp prop{};
+  std::string dev = "gpu";
+  if (cudaGetDeviceProperties(&prop, P->device) == cudaSuccess) dev = prop.name;
+  for (char& c : dev)
+    if (c == ' ') c = '_';
+  char buf[256];
+  snprintf(buf, sizeof(buf), "%s nx=%d ny=%d nk=%d nz=%d prec=%d J=%d table=%d", dev.c_str(),
+           P->nx, P->ny, P->nk, P->nz, P->p.precision, P->J, has_table ? 1 : 0);
+  return buf;
+}
+
+// Cached choice for `key` from the file named by ISAM_AUTOTUNE_CACHE: lines
+// "<key> -> tile=<t> stolt=<m>"; the last matching line wins.
+bool tune_cache_lookup(const std::string& key, int* tp, int* tab) {
+  const char* path = getenv("ISAM_AUTOTUNE_CACHE");
+  if (!path || !*path) return false;
+  FILE* f = fopen(path, "r");
+  if (!f) return false;
+  char line[512];
+  bool found = false;
+  const std::string head = key + " -> ";
+  while (fgets(line, sizeof(line), f)) {
+    if (strncmp(line, head.c_str(), head.size()) != 0) continue;
+    int t = 0, m = 0;
+    if (sscanf(line + head.size(), "tile=%d stolt=%d", &t, &m) == 2) {
+      *tp = t;
+      *tab = m;
+      found = true;
+    }
+  }
+  fclose(f);
+  return found;
+}
+
+void tune_cache_store(const std::string& key, int tp, int tab) {
+  const char* path = getenv("ISAM_AUTOTUNE_CACHE");
+  if (!path || !*path) return;
+  FILE* f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "%s -> tile=%d stolt=%d\n", key.c_str(), tp, tab);
+  fclose(f);
+}
+
 template <typename T> isam_status autotune_impl(isam_plan* P, int32_t* tile, int32_t* table) {
   Impl<T>& im = impl_of<T>(P);
+  {
+    // a cached choice that is still feasible for this plan is used as is
+    const std::string key = tune_key(P, im.tab.stab != nullptr);
+    const int Lc = P->ny == 1 ? P->nx : P->ny;
+    const int Mc = P->ny == 1 ? P->nz : P->nx * P->nz;
+    int t = 0, m = 0;
+    if (tune_cache_lookup(key, &t, &m) && (t == 1 || t == 2 || t == 4 || t == 8) &&
+        t <= Mc / 2 && (Lc >= 8 ? Lc / 8 : 1) * t <= 512 &&
+        (m == 0 || ((m == 1 || m == 2) && im.tab.stab))) {
+      P->tune_tp = t;
+      P->tune_table = m;
+      if (tile) *tile = t;
+      if (table) *table = m == 2 ? 0 : (im.tab.stab ? 1 : 0);
+      return ISAM_OK;
+    }
+  }
   if (!im.zA) ISAM_TRY(dalloc(&im.zA, P->n_img));
   if (!im.zB) ISAM_TRY(dalloc(&im.zB, P->n_img));
   if (!im.sdh) ISAM_TRY(dalloc(&im.sdh, P->n_spec));
@@ -1585,6 +1733,7 @@ template <typename T> isam_status autotune_impl(isam_plan* P, int32_t* tile, int
   P->prof = prof;
   P->tune_tp = st == ISAM_OK ? best_tp : 0;
   P->tune_table = st == ISAM_OK ? best_tab : 0;
+  if (st == ISAM_OK) tune_cache_store(tune_key(P, im.tab.stab != nullptr), best_tp, best_tab);
   if (tile) *tile = P->tune_tp;
   if (table) *table = P->tune_table == 2 ? 0 : (im.tab.stab ? 1 : 0);
   return st;

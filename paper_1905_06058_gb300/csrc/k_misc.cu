@@ -149,6 +149,52 @@ template cudaError_t launch_max_abs<double>(const double2*, size_t, double*, int
 template cudaError_t launch_norm2<float>(const float2*, size_t, double*, int, double*, cudaStream_t);
 template cudaError_t launch_norm2<double>(const double2*, size_t, double*, int, double*, cudaStream_t);
 
+// sum_i w[i mod nz] |x_i| (w null: 1), the l1 term of Eq. 12: per-block FP64
+// partials, then one block sums them in a fixed order into *out
+template <typename T>
+__global__ void __launch_bounds__(256) k_wl1(const cplx<T>* x, size_t n, const T* w, int nz,
+                                             double* partial) {
+  __shared__ double red[8];
+  double v = 0.0;
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += size_t(gridDim.x) * blockDim.x) {
+    const cplx<T> a = x[i];
+    const double m = sqrt(double(a.x) * a.x + double(a.y) * a.y);
+    v += w ? double(w[i & size_t(nz - 1)]) * m : m;
+  }
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = red[0];
+    for (int k = 1; k < int(blockDim.x >> 5); ++k) t += red[k];
+    partial[blockIdx.x] = t;
+  }
+}
+__global__ void __launch_bounds__(256) k_sum1(const double* partial, int n, double* out) {
+  __shared__ double red[256];
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v += partial[i];
+  red[threadIdx.x] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < int(blockDim.x); ++i) t += red[i];
+    *out = t;
+  }
+}
+template <typename T> cudaError_t launch_wl1(const cplx<T>* x, size_t n, const T* w, int nz,
+                                             double* partial, int nblocks, double* out,
+                                             cudaStream_t s) {
+  k_wl1<T><<<nblocks, 256, 0, s>>>(x, n, w, nz, partial);
+  k_sum1<<<1, 256, 0, s>>>(partial, nblocks, out);
+  return cudaGetLastError();
+}
+template cudaError_t launch_wl1<float>(const float2*, size_t, const float*, int, double*, int,
+                                       double*, cudaStream_t);
+template cudaError_t launch_wl1<double>(const double2*, size_t, const double*, int, double*, int,
+                                        double*, cudaStream_t);
+
 // out[0..2] = column sums of partial[n][3]
 __global__ void __launch_bounds__(256) k_sum3(const double* partial, int n, double* out) {
   __shared__ double red[3][256];

@@ -44,7 +44,8 @@ class SolveOpts(ctypes.Structure):
                 ("max_iter", ctypes.c_int32), ("tol", ctypes.c_double),
                 ("check_every", ctypes.c_int32), ("w_dev", ctypes.c_void_p),
                 ("residual_addback", ctypes.c_int32), ("L", ctypes.c_double),
-                ("eps", ctypes.c_double), ("prior", ctypes.c_int32)]
+                ("eps", ctypes.c_double), ("prior", ctypes.c_int32),
+                ("objective", ctypes.c_int32)]
 
 
 PRIORS = {"l1": 0, "haar_depth": 1}
@@ -57,10 +58,13 @@ class SolveState(ctypes.Structure):
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("rr", ctypes.c_double),
-                ("lambda_", ctypes.c_double), ("L", ctypes.c_double), ("status", ctypes.c_int32)]
+                ("lambda_", ctypes.c_double), ("L", ctypes.c_double), ("status", ctypes.c_int32),
+                ("objective", ctypes.c_double)]
 
 
 _P = ctypes.c_void_p
+_ALLOC_T = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE_T = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 _SIGS = {
     "isam_plan_create": (ctypes.c_int, [ctypes.POINTER(IsamParams), _P, ctypes.POINTER(_P)]),
     "isam_plan_destroy": (None, [_P]),
@@ -79,6 +83,7 @@ _SIGS = {
     "isam_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]),
     "isam_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "isam_set_allocator": (ctypes.c_int, [_P, _P, _P]),     # function pointers as void*
     "isam_dispersion_compensated_ifft": (ctypes.c_int, [_P, _P, _P]),
     "isam_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, ctypes.POINTER(_P),
                                          ctypes.POINTER(SolveOpts), ctypes.POINTER(_P), _P,
@@ -145,6 +150,42 @@ def _stream_handle(stream) -> int:
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
     return int(s.cuda_stream)
+
+
+# Every callback pair ever installed stays referenced: blocks are returned to
+# the allocator that made them, possibly after another one was installed.
+_ALLOCATORS = []
+
+
+def set_allocator(alloc=None, free=None) -> None:
+    """isam_set_allocator with Python callables: alloc(nbytes) -> device pointer
+    (int, 0 on failure), free(ptr).  No arguments restores cudaMalloc."""
+    if alloc is None and free is None:
+        _check(_lib.isam_set_allocator(None, None, None), "isam_set_allocator")
+        return
+
+    def _a(n, ctx):
+        try:
+            return alloc(int(n)) or None
+        except Exception:
+            return None
+
+    def _f(ptr, ctx):
+        try:
+            free(int(ptr))
+        except Exception:
+            pass
+    pair = (_ALLOC_T(_a), _FREE_T(_f))
+    _ALLOCATORS.append(pair)
+    _check(_lib.isam_set_allocator(ctypes.cast(pair[0], _P), ctypes.cast(pair[1], _P), None),
+           "isam_set_allocator")
+
+
+def use_torch_allocator() -> None:
+    """Plan workspace and tables from PyTorch's caching allocator."""
+    import torch
+    set_allocator(lambda n: torch.cuda.caching_allocator_alloc(n),
+                  lambda p: torch.cuda.caching_allocator_delete(p))
 
 
 class Plan:
@@ -235,9 +276,10 @@ class Plan:
         return out
 
     def _opts(self, lambda_rel, lambda_abs, max_iter, tol, check_every, w, addback, L, eps,
-              prior="l1"):
+              prior="l1", objective=False):
         o = SolveOpts()
         o.prior = PRIORS[prior]
+        o.objective = int(bool(objective))
         o.lambda_rel, o.lambda_abs = float(lambda_rel), float(lambda_abs)
         o.max_iter, o.tol, o.check_every = int(max_iter), float(tol), int(check_every)
         o.w_dev = None if w is None else self._dev(w, self.real_dtype, (self.image_shape[2],), "w")
@@ -247,7 +289,7 @@ class Plan:
 
     def solve(self, s, lambda_rel=0.01, lambda_abs=0.0, max_iter=100, tol=0.0, check_every=10,
               w=None, addback=False, L=0.0, eps=0.0, out=None, state: Optional[dict] = None,
-              prior: str = "l1"):
+              prior: str = "l1", objective: bool = False):
         """MBIR solve (Alg. 1).  Returns (eta, info dict).  ``state`` (optional) is a dict
         with CUDA tensors 'z1', 'z2' (images) and ints/floats 'k', 'lambda', 'L'; it is
         updated in place for checkpoint / resume."""
@@ -256,7 +298,7 @@ class Plan:
         if out is None:
             out = torch.empty(self.image_shape, dtype=self.cplx_dtype, device=s.device)
         o = self._opts(lambda_rel, lambda_abs, max_iter, tol, check_every, w, addback, L, eps,
-                       prior)
+                       prior, objective)
         info = SolveInfo()
         st_ptr = None
         if state is not None:
@@ -274,7 +316,7 @@ class Plan:
         if state is not None:
             state["k"], state["lambda"], state["L"] = st.k, st.lambda_, st.L
         return out, dict(iterations=info.iterations, rr=info.rr, lam=info.lambda_, L=info.L,
-                         status=info.status)
+                         status=info.status, objective=info.objective)
 
     def solve_host(self, s_host, out_host, lambda_rel=0.01, lambda_abs=0.0, max_iter=100,
                    tol=0.0, check_every=10, L=0.0, eps=0.0, addback=False):

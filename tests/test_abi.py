@@ -56,7 +56,8 @@ int main(void) {
   P(isam_params, flags)
   P(isam_solve_opts, max_iter) P(isam_solve_opts, w_dev) P(isam_solve_opts, L)
   P(isam_solve_opts, eps) P(isam_solve_opts, prior) P(isam_solve_state, k) P(isam_solve_state, L)
-  P(isam_solve_info, rr) P(isam_solve_info, status)
+  P(isam_solve_info, rr) P(isam_solve_info, status) P(isam_solve_info, objective)
+  P(isam_solve_opts, objective)
   return 0;
 }
 '''
@@ -124,3 +125,10 @@ def test_null_arguments(isam):
     assert lib.isam_solve(None, None, None, None, None, None) == 1
     assert lib.isam_last_launch_count(None) == -1
     lib.isam_plan_destroy(None)
+    a = isam._ALLOC_T(lambda n, c: None)
+    assert lib.isam_set_allocator(ctypes.cast(a, ctypes.c_void_p), None, None) == 1   # half a pair
+    assert lib.isam_set_allocator(None, None, None) == 0
+    assert lib.isam_batch_create(None, 0, None, None, None, None, None) == 1
+    assert lib.isam_set_filter(None, None) == 1
+    assert lib.isam_unrolled_checkpoint_images(20, 5) == 8
+    assert lib.isam_unrolled_checkpoint_images(0, 5) == -1
