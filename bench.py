@@ -515,9 +515,22 @@ def run_volume(torch):
     b.record()
     torch.cuda.synchronize()
     rate = it / (a.elapsed_time(b) / 1000.0)
+    # standalone A + A^H applications (C-ABI operators)
+    y = torch.empty(plan.spec_shape, dtype=torch.float32, device="cuda")
+    plan.forward(out, out=y)
+    plan.adjoint(y, out=out)
+    torch.cuda.synchronize()
+    reps = 5
+    a.record()
+    for _ in range(reps):
+        plan.forward(out, out=y)
+        plan.adjoint(y, out=out)
+    b.record()
+    torch.cuda.synchronize()
+    aah = reps / (a.elapsed_time(b) / 1000.0)
     n = wl.geom.nx * wl.geom.ny * wl.geom.nz
     plan.close()
-    return {"workload": wl.name, "iters_per_s": rate, "L_estimate_iters": 30,
+    return {"workload": wl.name, "iters_per_s": rate, "aah_per_s": aah, "L_estimate_iters": 30,
             "iteration_gbs_algorithmic": 60 * n * rate / 1e9}
 
 
