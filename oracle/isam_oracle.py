@@ -19,7 +19,8 @@ What it computes (paper section / equation in brackets):
 * adjoint  A^H y = K_hat^H y under the real inner product  [Eq. 17];
 * weighted complex soft threshold [Eq. 14], relative residual [Eq. 15],
   the prox of an l1 prior on orthonormal Haar detail coefficients along depth
-  (one of the other convex priors §3.1 names),
+  and of an isotropic total-variation prior (fast dual gradient projection)
+  (the other convex priors §3.1 names),
   FISTA [Alg. 1], residual add-back [Alg. 1, optional last step];
 * Lipschitz constant of the gradient by power iteration;
 * the optional filter B(q, k) of Eq. 3 (b of Eq. 16), as a table over |q|;
@@ -417,6 +418,66 @@ def haar_prox(u: np.ndarray, tau) -> np.ndarray:
     c = haar_forward(u)
     c[..., 1:] = soft_threshold(c[..., 1:], tau)
     return haar_inverse(c)
+
+
+def tv_grad(x: np.ndarray):
+    """Forward differences along x (axis -2) and z (axis -1), zero at the far
+    edge: (dx, dz) with dx[..., i, :] = x[..., i+1, :] - x[..., i, :]."""
+    dx = np.zeros_like(x)
+    dz = np.zeros_like(x)
+    dx[..., :-1, :] = x[..., 1:, :] - x[..., :-1, :]
+    dz[..., :, :-1] = x[..., :, 1:] - x[..., :, :-1]
+    return dx, dz
+
+
+def tv_grad_adjoint(px: np.ndarray, pz: np.ndarray) -> np.ndarray:
+    """Adjoint of tv_grad: <tv_grad(x), (px, pz)> = <x, tv_grad_adjoint(px, pz)>."""
+    out = np.zeros_like(px)
+    out[..., :-1, :] -= px[..., :-1, :]
+    out[..., 1:, :] += px[..., :-1, :]
+    out[..., :, :-1] -= pz[..., :, :-1]
+    out[..., :, 1:] += pz[..., :, :-1]
+    return out
+
+
+def total_variation(x: np.ndarray) -> float:
+    """Isotropic TV over (x, z) of every B-scan slice: sum sqrt(|dx|^2 + |dz|^2)."""
+    dx, dz = tv_grad(x)
+    return float(np.sum(np.sqrt(np.abs(dx) ** 2 + np.abs(dz) ** 2)))
+
+
+class TVProx:
+    """prox of tau TV (a total-variation prior, §3.1) by the fast gradient
+    projection on the dual (Beck & Teboulle): z = u - tau grad^H p with
+    |p| <= 1 per pixel; `iters` dual steps of size 1/(8 tau) per call, warm
+    started from the previous call's p (the dual state of a FISTA solve)."""
+
+    def __init__(self, iters: int = 20):
+        self.iters = iters
+        self.px = None
+        self.pz = None
+
+    def __call__(self, u: np.ndarray, tau: float) -> np.ndarray:
+        if self.px is None:
+            self.px = np.zeros_like(u, dtype=np.complex128)
+            self.pz = np.zeros_like(u, dtype=np.complex128)
+        px, pz = self.px, self.pz
+        rx, rz = px.copy(), pz.copy()
+        t = 1.0
+        for _ in range(self.iters):
+            w = u - tau * tv_grad_adjoint(rx, rz)
+            gx, gz = tv_grad(w)
+            qx = rx + gx / (8 * tau)
+            qz = rz + gz / (8 * tau)
+            m = np.maximum(1.0, np.sqrt(np.abs(qx) ** 2 + np.abs(qz) ** 2))
+            nx_, nz_ = qx / m, qz / m
+            t_next = (1 + math.sqrt(1 + 4 * t * t)) / 2
+            beta = (t - 1) / t_next
+            rx = nx_ + beta * (nx_ - px)
+            rz = nz_ + beta * (nz_ - pz)
+            px, pz, t = nx_, nz_, t_next
+        self.px, self.pz = px, pz
+        return u - tau * tv_grad_adjoint(px, pz)
 
 
 def relative_residual(z, eta, g, eps=1e-12) -> float:
