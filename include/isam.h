@@ -102,6 +102,7 @@ typedef struct {
   double eps;               /* r_r denominator guard (0: 1e-30)                   */
   int32_t prior;            /* ISAM_PRIOR_* (0: the weighted l1 of Eq. 12)         */
   int32_t objective;        /* 1: report the Eq. 12 objective of z^K in the info   */
+  int32_t prior_iters;      /* ISAM_PRIOR_TV: dual steps per prox (0: 20)          */
 } isam_solve_opts;
 
 /* Priors of the MBIR objective (§3.1: Eq. 12 extends to other convex priors):
@@ -109,9 +110,14 @@ typedef struct {
  * ISAM_PRIOR_HAAR_DEPTH: lambda ||details(W eta)||_1, W the orthonormal Haar
  *   transform along depth of every A-scan (all log2(nz) levels, the coarsest
  *   approximation coefficient unpenalised); prox = W^H T_{lambda/L}(W u).
- *   Needs w_dev = NULL and tol = 0 (ISAM_ERR_UNSUPPORTED otherwise); not
- *   available to the unrolled (calibration) entry points. */
-enum { ISAM_PRIOR_L1 = 0, ISAM_PRIOR_HAAR_DEPTH = 1 };
+ * ISAM_PRIOR_TV: lambda TV(eta), isotropic total variation over (x, z) of each
+ *   B-scan slice (forward differences, zero at the far edge); the prox is
+ *   found on its dual by fast gradient projection, prior_iters steps per
+ *   FISTA iteration, warm started from the previous iteration within a solve.
+ * Both need w_dev = NULL and tol = 0, and TV no resumed state (k > 0)
+ * (ISAM_ERR_UNSUPPORTED otherwise); neither is available to the unrolled
+ * (calibration) entry points. */
+enum { ISAM_PRIOR_L1 = 0, ISAM_PRIOR_HAAR_DEPTH = 1, ISAM_PRIOR_TV = 2 };
 
 /* Resumable solver state (checkpoint/restart).  z1 = z^{k}, z2 = z^{k-1} are
  * caller-owned device images; k iterations are done.  Pass k = 0 to start. */

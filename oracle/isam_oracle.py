@@ -458,9 +458,11 @@ class TVProx:
         self.pz = None
 
     def __call__(self, u: np.ndarray, tau: float) -> np.ndarray:
-        if self.px is None:
+        if self.px is None or tau <= 0:
             self.px = np.zeros_like(u, dtype=np.complex128)
             self.pz = np.zeros_like(u, dtype=np.complex128)
+        if tau <= 0:
+            return np.array(u, dtype=np.complex128)
         px, pz = self.px, self.pz
         rx, rz = px.copy(), pz.copy()
         t = 1.0

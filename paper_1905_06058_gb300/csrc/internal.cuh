@@ -167,6 +167,16 @@ template <typename T> cudaError_t launch_haar_prox(const cplx<T>* u, cplx<T>* z,
                                                    size_t n_ascans, T tau, const double* lam_dev,
                                                    double lam_scale, cudaStream_t s);
 
+// total-variation prox pieces (k_prior.cu); tau = lam_scale * (*lam_dev) when lam_dev
+template <typename T> cudaError_t launch_tv_primal(const cplx<T>* u, const cplx<T>* rx,
+                                                   const cplx<T>* rz, T tau, const double* lam_dev,
+                                                   double lam_scale, cplx<T>* w, int nx, int nz,
+                                                   size_t n, cudaStream_t s);
+template <typename T> cudaError_t launch_tv_dual(const cplx<T>* w, cplx<T>* px, cplx<T>* pz,
+                                                 cplx<T>* rx, cplx<T>* rz, T tau,
+                                                 const double* lam_dev, double lam_scale, T beta,
+                                                 int nx, int nz, size_t n, cudaStream_t s);
+
 // Eq. 9 direct reconstruction (k_direct.cu)
 template <typename T> cudaError_t launch_dc_ifft(const T* s, cplx<T>* out, const cplx<T>* disp,
                                                  const cplx<T>* post, int nk, int nz, int lognz,

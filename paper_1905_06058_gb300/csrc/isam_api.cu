@@ -46,6 +46,7 @@ template <typename T> struct Impl {
   int seg_cap = 0;
   cplx<T>* cal = nullptr;       // [5][n_img]: zbar x 3, ubar, b
   cplx<T>* dc_post = nullptr;   // [nz] output phase of the Eq. 9 reconstruction
+  cplx<T>* tv = nullptr;        // [5][n_img]: TV dual p_x, p_z, momentum r_x, r_z, primal w
   bool ready = false;
 };
 
@@ -217,7 +218,7 @@ template <typename T> void impl_free(Impl<T>& im) {
   dfree(im.eta_hat); dfree(im.spec); dfree(im.grad); dfree(im.sdh);
   dfree(im.zA); dfree(im.zB); dfree(im.s_tmp);
   dfree(im.s_host_stage); dfree(im.out_stage);
-  dfree(im.spec2); dfree(im.seg); dfree(im.cal); dfree(im.dc_post);
+  dfree(im.spec2); dfree(im.seg); dfree(im.cal); dfree(im.dc_post); dfree(im.tv);
   im = Impl<T>();
 }
 
@@ -447,14 +448,15 @@ template <typename T> isam_status fista_iteration(isam_plan* P, Impl<T>& im,
                                                   cplx<T>* u_out = nullptr,
                                                   const double* lam_dev = nullptr,
                                                   double lam_scale = 0.0,
-                                                  int prior = ISAM_PRIOR_L1) {
+                                                  int prior = ISAM_PRIOR_L1,
+                                                  int prior_iters = 0) {
   cudaStream_t s = P->stream;
   if (!ehat_in) ehat_in = im.eta_hat;
   if (!ehat_out) ehat_out = im.eta_hat;
   AxArgs<T> ax = ax_args<T>(P, im, ehat_in, im.grad);
   ax.sdh = im.sdh;
   ISAM_TRY(launch(P, ISAM_KCLASS_AX_FUSED, [&] { return launch_ax_fused<T>(ax, P->npairs, s); }));
-  if (prior == ISAM_PRIOR_HAAR_DEPTH) {
+  if (prior == ISAM_PRIOR_HAAR_DEPTH || prior == ISAM_PRIOR_TV) {
     // u^k = eta^k - g/L in image space (in place over G_hat), the Haar prox to
     // z^k, then eta_hat^{k+1} = F(z^k + mu_k (z^k - z^{k-1}))
     LatArgs<T> g;
@@ -466,10 +468,42 @@ template <typename T> isam_status fista_iteration(isam_plan* P, Impl<T>& im,
     }
     g.z1 = z1; g.z2 = z2; g.inv_L = T(1.0 / L); g.mu_prev = T(mu_prev); g.flag = P->flag;
     ISAM_TRY(lat<T>(P, LAT_GRAD_STEP, g));
-    ISAM_TRY(launch(P, ISAM_KCLASS_MISC, [&] {
-      return launch_haar_prox<T>(im.grad, zout, P->nz, size_t(P->nx) * P->ny, T(lam / L), lam_dev,
-                                 lam_scale, s);
-    }));
+    if (prior == ISAM_PRIOR_HAAR_DEPTH) {
+      ISAM_TRY(launch(P, ISAM_KCLASS_MISC, [&] {
+        return launch_haar_prox<T>(im.grad, zout, P->nz, size_t(P->nx) * P->ny, T(lam / L),
+                                   lam_dev, lam_scale, s);
+      }));
+    } else {
+      // TV prox of u = im.grad: the dual (p) carries over from the previous
+      // iteration; r starts at p; fast gradient projection; z = u - tau grad^H p
+      const size_t n = P->n_img;
+      cplx<T>* px = im.tv;
+      cplx<T>* pz = im.tv + n;
+      cplx<T>* rx = im.tv + 2 * n;
+      cplx<T>* rz = im.tv + 3 * n;
+      cplx<T>* w = im.tv + 4 * n;
+      const T tau = T(lam / L);
+      CUDA_TRY(cudaMemcpyAsync(rx, px, 2 * n * sizeof(cplx<T>), cudaMemcpyDeviceToDevice, s));
+      double t = 1.0;
+      const int iters = prior_iters > 0 ? prior_iters : 20;
+      for (int i = 0; i < iters; ++i) {
+        const double t_next = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+        const T beta = T((t - 1.0) / t_next);
+        t = t_next;
+        ISAM_TRY(launch(P, ISAM_KCLASS_MISC, [&] {
+          return launch_tv_primal<T>(im.grad, rx, rz, tau, lam_dev, lam_scale, w, P->nx, P->nz, n,
+                                     s);
+        }));
+        ISAM_TRY(launch(P, ISAM_KCLASS_MISC, [&] {
+          return launch_tv_dual<T>(w, px, pz, rx, rz, tau, lam_dev, lam_scale, beta, P->nx, P->nz,
+                                   n, s);
+        }));
+      }
+      ISAM_TRY(launch(P, ISAM_KCLASS_MISC, [&] {
+        return launch_tv_primal<T>(im.grad, px, pz, tau, lam_dev, lam_scale, zout, P->nx, P->nz,
+                                   n, s);
+      }));
+    }
     LatArgs<T> e = lat_args<T>(P->ny, P->nx, P->nz, nullptr, ehat_out);
     e.z1 = zout; e.z2 = z1; e.mu = T(mu);
     ISAM_TRY(lat<T>(P, LAT_EXTRAP_FWD, e));
@@ -562,6 +596,10 @@ template <typename T> isam_status solve_impl(isam_plan* P, const T* s_d, const i
     CUDA_TRY(cudaMemsetAsync(zQ, 0, sizeof(cplx<T>) * P->n_img, s));
     CUDA_TRY(cudaMemsetAsync(im.eta_hat, 0, sizeof(cplx<T>) * P->n_img, s));
   }
+  if (o->prior == ISAM_PRIOR_TV) {                 // TV dual starts at 0 for every solve
+    if (!im.tv) ISAM_TRY(dalloc(&im.tv, 5 * P->n_img));
+    CUDA_TRY(cudaMemsetAsync(im.tv, 0, 2 * sizeof(cplx<T>) * P->n_img, s));
+  }
   // lateral spectrum of the data, used by every iteration's residual
   if (!im.sdh) ISAM_TRY(dalloc(&im.sdh, P->n_spec));
   ISAM_TRY(lat_forward<T>(P, im, s_d, im.sdh, P->nk, true));
@@ -575,7 +613,7 @@ template <typename T> isam_status solve_impl(isam_plan* P, const T* s_d, const i
     const bool norms = check && (it % every == 0 || it == o->max_iter);
     ISAM_TRY(fista_iteration<T>(P, im, zP, zQ, zQ, static_cast<const T*>(o->w_dev), lam, L,
                                 mu[k - 1], mu[k], norms, nullptr, nullptr, nullptr, nullptr, 0.0,
-                                o->prior));
+                                o->prior, o->prior_iters));
     std::swap(zP, zQ);   // zP = z^k, zQ = z^{k-1}
     done = it;
     if (norms) {
@@ -922,8 +960,10 @@ static isam_status check_opts(const isam_plan* P, const isam_solve_opts* o) {
   if (o->max_iter < 1) return ISAM_ERR_INVALID;
   if (!(o->lambda_abs > 0) && !(o->lambda_rel >= 0)) return ISAM_ERR_INVALID;
   if (o->tol < 0 || !isfinite(o->tol)) return ISAM_ERR_INVALID;
-  if (o->prior != ISAM_PRIOR_L1 && o->prior != ISAM_PRIOR_HAAR_DEPTH) return ISAM_ERR_INVALID;
-  if (o->prior == ISAM_PRIOR_HAAR_DEPTH && (o->w_dev || o->tol > 0)) return ISAM_ERR_UNSUPPORTED;
+  if (o->prior != ISAM_PRIOR_L1 && o->prior != ISAM_PRIOR_HAAR_DEPTH && o->prior != ISAM_PRIOR_TV)
+    return ISAM_ERR_INVALID;
+  if (o->prior_iters < 0) return ISAM_ERR_INVALID;
+  if (o->prior != ISAM_PRIOR_L1 && (o->w_dev || o->tol > 0)) return ISAM_ERR_UNSUPPORTED;
   (void)P;
   return ISAM_OK;
 }
@@ -933,6 +973,7 @@ isam_status isam_solve(isam_plan* P, const void* s_d, const isam_solve_opts* o, 
   if (!P || !s_d || !eta_out) return ISAM_ERR_INVALID;
   ISAM_TRY(check_opts(P, o));
   if (state && (!state->z1 || !state->z2 || state->k < 0)) return ISAM_ERR_INVALID;
+  if (state && state->k > 0 && o->prior == ISAM_PRIOR_TV) return ISAM_ERR_UNSUPPORTED;
   DeviceGuard g(P->device);
   P->launches = 0;
   if (P->p.precision == ISAM_FP64)
@@ -1402,6 +1443,7 @@ template <typename T> isam_status batch_prepare(isam_plan* P, const isam_solve_o
   if (!im.zB) ISAM_TRY(dalloc(&im.zB, P->n_img));
   if (!im.sdh) ISAM_TRY(dalloc(&im.sdh, P->n_spec));
   if (!im.s_tmp) ISAM_TRY(dalloc(&im.s_tmp, P->n_spec));
+  if (o->prior == ISAM_PRIOR_TV && !im.tv) ISAM_TRY(dalloc(&im.tv, 5 * P->n_img));
   double L = o->L;
   if (!(L > 0)) {
     if (!(P->L_cache > 0)) {
@@ -1444,6 +1486,7 @@ template <typename T> isam_status batch_enqueue(isam_plan* P, const T* s_d,
   CUDA_TRY(cudaMemsetAsync(im.zA, 0, bytes, s));
   CUDA_TRY(cudaMemsetAsync(im.zB, 0, bytes, s));
   CUDA_TRY(cudaMemsetAsync(im.eta_hat, 0, bytes, s));
+  if (o->prior == ISAM_PRIOR_TV) CUDA_TRY(cudaMemsetAsync(im.tv, 0, 2 * bytes, s));
   std::vector<double> mu;
   momentum(o->max_iter + 1, mu);
   cplx<T>* zP = im.zA;
@@ -1451,7 +1494,7 @@ template <typename T> isam_status batch_enqueue(isam_plan* P, const T* s_d,
   const T* w = static_cast<const T*>(o->w_dev);
   for (int k = 1; k <= o->max_iter; ++k) {
     ISAM_TRY(fista_iteration<T>(P, im, zP, zQ, zQ, w, lam, L, mu[k - 1], mu[k], false, nullptr,
-                                nullptr, nullptr, lam_dev, lam_scale, o->prior));
+                                nullptr, nullptr, lam_dev, lam_scale, o->prior, o->prior_iters));
     std::swap(zP, zQ);
   }
   if (o->residual_addback) {

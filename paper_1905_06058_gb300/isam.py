@@ -45,10 +45,10 @@ class SolveOpts(ctypes.Structure):
                 ("check_every", ctypes.c_int32), ("w_dev", ctypes.c_void_p),
                 ("residual_addback", ctypes.c_int32), ("L", ctypes.c_double),
                 ("eps", ctypes.c_double), ("prior", ctypes.c_int32),
-                ("objective", ctypes.c_int32)]
+                ("objective", ctypes.c_int32), ("prior_iters", ctypes.c_int32)]
 
 
-PRIORS = {"l1": 0, "haar_depth": 1}
+PRIORS = {"l1": 0, "haar_depth": 1, "tv": 2}
 
 
 class SolveState(ctypes.Structure):
@@ -276,9 +276,10 @@ class Plan:
         return out
 
     def _opts(self, lambda_rel, lambda_abs, max_iter, tol, check_every, w, addback, L, eps,
-              prior="l1", objective=False):
+              prior="l1", objective=False, prior_iters=0):
         o = SolveOpts()
         o.prior = PRIORS[prior]
+        o.prior_iters = int(prior_iters)
         o.objective = int(bool(objective))
         o.lambda_rel, o.lambda_abs = float(lambda_rel), float(lambda_abs)
         o.max_iter, o.tol, o.check_every = int(max_iter), float(tol), int(check_every)
@@ -289,7 +290,7 @@ class Plan:
 
     def solve(self, s, lambda_rel=0.01, lambda_abs=0.0, max_iter=100, tol=0.0, check_every=10,
               w=None, addback=False, L=0.0, eps=0.0, out=None, state: Optional[dict] = None,
-              prior: str = "l1", objective: bool = False):
+              prior: str = "l1", objective: bool = False, prior_iters: int = 0):
         """MBIR solve (Alg. 1).  Returns (eta, info dict).  ``state`` (optional) is a dict
         with CUDA tensors 'z1', 'z2' (images) and ints/floats 'k', 'lambda', 'L'; it is
         updated in place for checkpoint / resume."""
@@ -298,7 +299,7 @@ class Plan:
         if out is None:
             out = torch.empty(self.image_shape, dtype=self.cplx_dtype, device=s.device)
         o = self._opts(lambda_rel, lambda_abs, max_iter, tol, check_every, w, addback, L, eps,
-                       prior, objective)
+                       prior, objective, prior_iters)
         info = SolveInfo()
         st_ptr = None
         if state is not None:
@@ -471,7 +472,7 @@ class Batch:
             opts[i] = plan._opts(kw.get("lambda_rel", 0.01), kw.get("lambda_abs", 0.0),
                                  kw.get("max_iter", 100), 0.0, 1, kw.get("w"),
                                  kw.get("addback", False), kw.get("L", 0.0), 0.0,
-                                 kw.get("prior", "l1"))
+                                 kw.get("prior", "l1"), False, kw.get("prior_iters", 0))
             self._keep.append((plan, s, out, kw.get("w")))
         self.n = n
         h = _P()

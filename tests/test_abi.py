@@ -57,7 +57,7 @@ int main(void) {
   P(isam_solve_opts, max_iter) P(isam_solve_opts, w_dev) P(isam_solve_opts, L)
   P(isam_solve_opts, eps) P(isam_solve_opts, prior) P(isam_solve_state, k) P(isam_solve_state, L)
   P(isam_solve_info, rr) P(isam_solve_info, status) P(isam_solve_info, objective)
-  P(isam_solve_opts, objective)
+  P(isam_solve_opts, objective) P(isam_solve_opts, prior_iters)
   return 0;
 }
 '''

@@ -1,7 +1,7 @@
-"""The Haar-depth prior (ISAM_PRIOR_HAAR_DEPTH) against the oracle's FISTA
-with the Haar prox: within 1e-3 (FP32) / 1e-6 (FP64) after the stated
-iterations; refused with weights, with a stop rule and for unknown priors;
-a batch entry with the prior equals its plan's solve."""
+"""The Haar-depth and TV priors against the oracle's FISTA with the same
+prox: within 1e-3 (FP32) / 1e-6 (FP64) after the stated iterations; refused
+with weights, with a stop rule (and, for TV, a resumed state); a batch entry
+with the prior equals its plan's solve."""
 import numpy as np
 import pytest
 
@@ -69,6 +69,52 @@ def test_haar_prior_refusals_and_batch(torch):
     b = Batch([(plan, sd, out, dict(lambda_rel=0.03, L=L, max_iter=25, prior="haar_depth"))])
     info = b.run()
     assert info[0]["status"] == 0
+    assert rel(out.cpu().numpy(), ref.cpu().numpy()) < 1e-5
+    b.close()
+    plan.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-3), ("fp64", 1e-6)])
+@pytest.mark.parametrize("kw", [dict(nx=32, nk=64, nz=128), dict(nx=8, ny=4, nk=32, nz=64)],
+                         ids=["bscan", "volume"])
+def test_tv_prior_solve_matches_oracle(torch, prec, tol, kw):
+    """Isotropic TV over (x, z): the oracle runs the same fast dual gradient
+    projection (10 steps per prox, warm started) inside its FISTA."""
+    from paper_1905_06058_gb300.isam import Plan
+    wl, op, s, L = problem(42, **kw)
+    lam = O.lambda_from_data(op.adjoint, s, 0.02)
+    ref = O.fista(op.forward, op.adjoint, s, lam, L, max_iter=20, shape=op.image_shape,
+                  prox=O.TVProx(10))
+    dt = np.float64 if prec == "fp64" else np.float32
+    plan = Plan(wl.geom, precision=prec)
+    sd = torch.from_numpy(s.astype(dt)).cuda()
+    out, info = plan.solve(sd, lambda_abs=lam, L=L, max_iter=20, prior="tv", prior_iters=10)
+    plan.close()
+    assert rel(out.cpu().numpy(), ref.eta) < tol
+    l1 = O.fista(op.forward, op.adjoint, s, lam, L, max_iter=20, shape=op.image_shape)
+    assert rel(l1.eta, ref.eta) > 10 * tol
+
+
+def test_tv_prior_refusals_and_batch(torch):
+    from paper_1905_06058_gb300.isam import Batch, IsamError, Plan
+    wl, op, s, L = problem(43, nx=16, nk=64, nz=64)
+    plan = Plan(wl.geom)
+    sd = torch.from_numpy(s.astype(np.float32)).cuda()
+    w = torch.ones(64, dtype=torch.float32, device="cuda")
+    for kw in (dict(w=w), dict(tol=1e-3)):
+        with pytest.raises(IsamError) as e:
+            plan.solve(sd, L=L, max_iter=5, prior="tv", **kw)
+        assert e.value.status == 6
+    st = {"z1": torch.zeros(plan.image_shape, dtype=torch.complex64, device="cuda"),
+          "z2": torch.zeros(plan.image_shape, dtype=torch.complex64, device="cuda"), "k": 3}
+    with pytest.raises(IsamError) as e:
+        plan.solve(sd, L=L, max_iter=5, prior="tv", state=st)
+    assert e.value.status == 6
+    ref, _ = plan.solve(sd, lambda_rel=0.02, L=L, max_iter=15, prior="tv", prior_iters=8)
+    out = torch.empty_like(ref)
+    b = Batch([(plan, sd, out, dict(lambda_rel=0.02, L=L, max_iter=15, prior="tv",
+                                    prior_iters=8))])
+    assert b.run()[0]["status"] == 0
     assert rel(out.cpu().numpy(), ref.cpu().numpy()) < 1e-5
     b.close()
     plan.close()
