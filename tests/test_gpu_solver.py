@@ -255,3 +255,24 @@ def test_evanescent_geometry_solve(torch):
     out, info = plan.solve(dev(torch, s, np.float64), lambda_abs=lam, L=L, max_iter=30)
     assert rel(out.cpu().numpy(), res.eta) < 1e-6
     plan.close()
+
+
+@pytest.mark.slow
+def test_config3_subvolume_reconstruction(torch):
+    """The volume workload on a 64 x 64 x 256 sub-volume (points, curved layers,
+    1% speckle, 25 dB): 150 iterations, lambda = 0.02 ||A^H y||_inf, FP32, within
+    1e-3 of the oracle's FISTA (L from 30 oracle power iterations, given to both)."""
+    from paper_1905_06058_gb300.isam import Plan
+    wl = I.config3(dtype=np.complex128, nx=64, nk=256, n_points=300)
+    ref = O.IsamOracle(wl.geom, "nufft")
+    s = I.add_noise(ref.forward(wl.eta), wl.snr_db, np.random.default_rng(wl.seed))
+    L = 1.01 * O.power_iteration(ref.forward, ref.adjoint, I.start_vector(ref.image_shape, 3), 30,
+                                 1e-6)
+    lam = O.lambda_from_data(ref.adjoint, s, wl.lambda_rel)
+    res = O.fista(ref.forward, ref.adjoint, s, lam, L, max_iter=wl.iters, shape=ref.image_shape)
+    plan = Plan(wl.geom, precision="fp32")
+    out, info = plan.solve(dev(torch, s, np.float32), lambda_rel=wl.lambda_rel, L=L,
+                           max_iter=wl.iters)
+    plan.close()
+    assert info["lam"] == pytest.approx(lam, rel=1e-5)
+    assert rel(out.cpu().numpy(), res.eta) < 1e-3
