@@ -284,7 +284,10 @@ isam_status isam_fista_unrolled_vjp(isam_plan* plan, const void* s_d,
  * legacy default stream (capture is not allowed there); NULL makes the batch
  * create its own.  Run: launches the graph on that stream, waits, and fills
  * info[i] (nullable; rr = -1); returns the first non-OK entry status.  The
- * caller orders earlier work on s_d before the run (e.g. synchronises). */
+ * caller orders earlier work on s_d before the run (e.g. synchronises).
+ * The graph records the plans' tables and launch shapes: while a batch
+ * exists, isam_set_model, isam_set_filter and isam_autotune on its plans
+ * return ISAM_ERR_INVALID, and the plans must not be destroyed. */
 typedef struct isam_batch isam_batch;
 isam_status isam_batch_create(isam_plan* const* plans, int32_t n, const void* const* s_d,
                               const isam_solve_opts* opts, void* const* eta_out, void* stream,

@@ -74,6 +74,7 @@ struct isam_plan {
   // and whether the fused kernel reads the Stolt table (1) or evaluates (2)
   int tune_tp = 0;
   int tune_table = 0;
+  int batch_refs = 0;           // batches whose graph records this plan's kernels
   // filter B of Eq. 3 per |q| class, interleaved (re, im); empty: B = 1
   std::vector<double> filt_host;
   double* cpartial = nullptr;   // [npairs][5] calibration partial sums
@@ -1293,6 +1294,7 @@ extern "C" {
 isam_status isam_set_model(isam_plan* P, int32_t n_disp, const double* disp, double z0) {
   if (!P || n_disp < 0 || n_disp > 4 || (n_disp > 0 && !disp) || !isfinite(z0))
     return ISAM_ERR_INVALID;
+  if (P->batch_refs) return ISAM_ERR_INVALID;       // a batch graph records the plan
   for (int i = 0; i < n_disp; ++i)
     if (!isfinite(disp[i])) return ISAM_ERR_INVALID;
   DeviceGuard g(P->device);
@@ -1309,6 +1311,7 @@ isam_status isam_set_model(isam_plan* P, int32_t n_disp, const double* disp, dou
 
 isam_status isam_set_filter(isam_plan* P, const double* b) {
   if (!P) return ISAM_ERR_INVALID;
+  if (P->batch_refs) return ISAM_ERR_INVALID;       // a batch graph records the plan
   const size_t n = 2 * size_t(P->ny / 2 + 1) * (P->nx / 2 + 1) * P->nk;
   if (b)
     for (size_t i = 0; i < n; ++i)
@@ -1603,6 +1606,7 @@ isam_status isam_batch_create(isam_plan* const* plans, int32_t n, const void* co
     batch_free(B);
     return st;
   }
+  for (isam_plan* P : B->plans) ++P->batch_refs;
   *out = B;
   return ISAM_OK;
 }
@@ -1644,6 +1648,7 @@ void isam_batch_destroy(isam_batch* B) {
   if (!B) return;
   DeviceGuard g(B->device);
   cudaStreamSynchronize(B->origin);
+  for (isam_plan* P : B->plans) --P->batch_refs;
   batch_free(B);
 }
 
@@ -1788,6 +1793,7 @@ extern "C" {
 
 isam_status isam_autotune(isam_plan* P, int32_t* tile, int32_t* stolt_table) {
   if (!P) return ISAM_ERR_INVALID;
+  if (P->batch_refs) return ISAM_ERR_INVALID;       // a batch graph records the plan
   DeviceGuard g(P->device);
   P->launches = 0;
   if (P->p.precision == ISAM_FP64) return autotune_impl<double>(P, tile, stolt_table);

@@ -104,3 +104,23 @@ def test_batch_refusals_and_nonfinite_entry(torch):
     infos = b.run()
     assert [i["status"] for i in infos] == [0, 4, 0]
     b.close()
+
+
+def test_batch_pins_its_plans(torch):
+    """While a batch's graph records a plan, calls that would change the
+    recorded tables or shapes are refused; after destroy they work again."""
+    from paper_1905_06058_gb300.isam import Batch, IsamError
+    ents = entries(torch, seed0=80)[:2]
+    p, sd, res, kw = ents[0][:4]
+    b = Batch([(e[0], e[1], e[2], e[3]) for e in ents])
+    g = ents[0][4].geom
+    for call in (lambda: p.set_model(g.disp, g.z0), lambda: p.set_filter(None), p.autotune):
+        with pytest.raises(IsamError) as e:
+            call()
+        assert e.value.status == 1
+    b.run()
+    b.close()
+    p.set_model(g.disp, g.z0)
+    p.autotune()
+    for e in ents:
+        e[0].close()
