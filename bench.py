@@ -48,7 +48,7 @@ def parse_args():
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the built-in launch shapes (for runs under a profiler)")
     ap.add_argument("--batch-iters", type=int, default=200)
-    ap.add_argument("--calib-steps", type=int, default=10,
+    ap.add_argument("--calib-steps", type=int, default=50,
                     help="Adam steps timed in the calibration line")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--L", type=float, default=0.0,
