@@ -430,6 +430,12 @@ __global__ void __launch_bounds__(512, 2) k_ax_fused(const __grid_constant__ AxA
   pair_columns(A, c1, c2, mx, my);
   const bool two = c2 != c1;
   if (tid == 0) { ch_lo = INT_MAX; ch_hi = INT_MIN; }
+  // Programmatic dependent launch: the next kernel in the stream may start its
+  // own prologue on SMs this grid leaves idle; this grid builds its twiddles,
+  // then waits for the previous kernel before touching global data.
+  cudaTriggerProgrammaticLaunchCompletion();
+  build_twiddles<T>(tw, K, sc.logK);
+  cudaGridDependencySynchronize();
   // F s_d at this pair's samples, fetched before the transforms need them
   const C* d1 = A.sdh + size_t(c1) * nk;
   C dqv[NRES];
@@ -438,7 +444,6 @@ __global__ void __launch_bounds__(512, 2) k_ax_fused(const __grid_constant__ AxA
     const int j = NRES * tid + rho;
     dqv[rho] = j < nk ? d1[j] : mk<T>(0, 0);
   }
-  build_twiddles<T>(tw, K, sc.logK);
   load_and_fft(A, Y, tw, c1, c2, two);
 
   const Positions<T> pos(A, mx, my);
@@ -549,7 +554,18 @@ static cudaError_t launch_ax_J(const AxArgs<T>& a, int npairs, cudaStream_t s, i
     k_ax_fwd<T, J><<<npairs, threads, sm, s>>>(a);
   } else {
     cudaFuncSetAttribute(k_ax_fused<T, J>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-    k_ax_fused<T, J><<<npairs, threads, sm, s>>>(a);
+    // programmatic dependent launch (see k_ax_fused's prologue)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(npairs);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_ax_fused<T, J>, a);
   }
   return cudaGetLastError();
 }

@@ -73,7 +73,11 @@ __global__ void __launch_bounds__(512, 2) k_lat(const __grid_constant__ LatArgs<
   const int tid = threadIdx.x, nt = blockDim.x;
   const int TP = a.TZ, L = a.L, logTP = a.logTZ;
   cplx<T>* tw = reinterpret_cast<cplx<T>*>(buf + size_t(padded_rows(L)) * TP);
+  // programmatic dependent launch: let the next kernel start its prologue,
+  // build the twiddles, then wait for the previous kernel's results
+  cudaTriggerProgrammaticLaunchCompletion();
   build_twiddles<T>(tw, L, a.logL, a.r3);
+  cudaGridDependencySynchronize();
   const int col = tid & (TP - 1), b = tid >> logTP;
   const size_t M = size_t(a.M);
   const size_t m_first = size_t(blockIdx.x) * (2 * TP);
@@ -310,8 +314,17 @@ static cudaError_t launch_lat_mode(const LatArgs<T>& a, cudaStream_t s) {
   const size_t sm = lat_smem_bytes<T>(a.L, a.TZ);
   cudaFuncSetAttribute(k_lat<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
   dim3 grid(a.M / (2 * a.TZ), a.B);
-  k_lat<T, MODE><<<grid, threads, sm, s>>>(a);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_lat<T, MODE>, a);
 }
 
 template <typename T> cudaError_t launch_lat(int mode, const LatArgs<T>& a, cudaStream_t s) {
