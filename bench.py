@@ -436,12 +436,18 @@ def run_calibration(torch, steps: int):
     scale = calib.theta_scales(wl.geom)
     truth = np.array(list(wl.geom.disp) + [wl.geom.z0])
     err = lambda th: [float(abs(th[i] - truth[i]) / scale[i]) for i in (1, 2, 4)]
+    norm = sum(float(torch.sum(s.double() ** 2)) for s in spectra)
+    th = torch.from_numpy(truth)
+    truth_loss = sum(float(calib.data_fidelity(s, th, plan, lm, L, wl.K, wl.every))
+                     for s, lm in zip(spectra, lams)) / norm
     plan.close()
     return {"workload": wl.name, "K": wl.K, "checkpoint_every": wl.every, "steps": steps,
             "adam_steps_per_s": steps / res.seconds,
             "ms_per_bscan_step": res.seconds / steps / len(spectra) * 1e3,
-            "loss_first": res.losses[0], "loss_last": res.losses[-1],
+            "loss_first": res.losses[0], "loss_last": res.losses[-1], "loss_best": res.best_loss,
+            "loss_at_hidden_theta": truth_loss,
             "theta_error_start_a2_a3_z0": err(wl.start), "theta_error_end_a2_a3_z0": err(res.theta),
+            "theta_error_best_a2_a3_z0": err(res.best_theta),
             "units": "a_i: rad at the band edge; z0: fraction of the depth range"}
 
 

@@ -130,9 +130,11 @@ def data_fidelity(s_d, theta, plan: Plan, lam: float, L: float, K: int, every: i
 
 @dataclass
 class CalibResult:
-    theta: np.ndarray        # fitted (a1..a4, z0)
-    losses: list             # normalised data fidelity per step
+    theta: np.ndarray        # theta after the last step
+    losses: list             # normalised data fidelity per step, at the theta the step started from
     seconds: float           # wall time of the steps
+    best_theta: np.ndarray   # the theta with the lowest loss seen
+    best_loss: float
 
 
 def theta_scales(geom) -> np.ndarray:
@@ -144,18 +146,31 @@ def theta_scales(geom) -> np.ndarray:
 
 
 def calibrate(plan: Plan, spectra: list, theta0, lam: list, L: float, K: int = 20,
-              every: int = 5, steps: int = 50, lr: float = 1e-2, fit=(1, 2, 4)) -> CalibResult:
+              every: int = 5, steps: int = 50, lr: float = 5e-2, fit=(1, 2, 4),
+              lr_final: float = 0.02, z0_step: float = 1 / 32) -> CalibResult:
     """Adam on the normalised data fidelity summed over `spectra` (device tensors
-    of one geometry), moving the components `fit` of theta (default a2, a3, z0)."""
+    of one geometry), moving the components `fit` of theta (default a2, a3, z0).
+
+    The step size follows a half cosine from lr down to lr * lr_final over the
+    steps (lr_final = 1 keeps it constant): the fidelity through the unrolled
+    solve is not convex in the phase coefficients, and a constant step keeps
+    Adam bouncing across the valley it has found.  Adam moves every component
+    by about the step size in its own unit; z0 moves in units of z0_step of
+    the depth range, a_i in radians at the band edge (theta_scales), so that
+    one step shifts the focus by a fraction of a depth pixel, not by tens."""
     import time
     scale = torch.from_numpy(theta_scales(plan.geom))
+    scale[4] *= z0_step
     base = torch.as_tensor(np.asarray(theta0, dtype=np.float64))
     mask = torch.zeros(N_PARAMS, dtype=torch.float64)
     mask[list(fit)] = 1.0
     p = torch.zeros(N_PARAMS, dtype=torch.float64, requires_grad=True)
     opt = torch.optim.Adam([p], lr=lr)
+    anneal = lambda i: lr_final + (1.0 - lr_final) * 0.5 * (1.0 + math.cos(math.pi * i / max(steps, 1)))
+    sched = torch.optim.lr_scheduler.LambdaLR(opt, anneal)
     norm = sum(float(torch.sum(s.double() ** 2)) for s in spectra)
     losses = []
+    best_theta, best_loss = base.numpy().copy(), math.inf
     t0 = time.perf_counter()
     for _ in range(steps):
         opt.zero_grad()
@@ -163,9 +178,13 @@ def calibrate(plan: Plan, spectra: list, theta0, lam: list, L: float, K: int = 2
         loss = sum(data_fidelity(s, theta, plan, lm, L, K, every) for s, lm in zip(spectra, lam))
         loss = loss / norm
         loss.backward()
+        value = float(loss.detach())
+        if value < best_loss:
+            best_theta, best_loss = theta.detach().numpy().copy(), value
         opt.step()
-        losses.append(float(loss.detach()))
+        sched.step()
+        losses.append(value)
     torch.cuda.synchronize()
     seconds = time.perf_counter() - t0
     theta = (base + mask * p.detach() * scale).numpy()
-    return CalibResult(theta, losses, seconds)
+    return CalibResult(theta, losses, seconds, best_theta, best_loss)

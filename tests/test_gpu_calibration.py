@@ -227,9 +227,11 @@ def test_calibration_recovers_hidden_theta(torch):
     start[1] += 0.6 * scale[1]
     start[2] -= 0.4 * scale[2]
     start[4] += 0.01 * scale[4]
-    res = calib.calibrate(plan, spectra, start, lams, L, K=20, every=5, steps=60, lr=2e-2)
+    res = calib.calibrate(plan, spectra, start, lams, L, K=20, every=5, steps=60)
     plan.close()
     err0 = np.abs((start - truth) / scale)[[1, 2, 4]]
     err1 = np.abs((res.theta - truth) / scale)[[1, 2, 4]]
     assert res.losses[-1] < 0.5 * res.losses[0]
-    assert np.all(err1 < 0.5 * err0), (err0, err1)
+    # the annealed step settles: the last loss is within 5 % of the best seen
+    assert res.losses[-1] <= 1.05 * res.best_loss, (res.losses[-1], res.best_loss)
+    assert np.all(err1 < 0.2 * err0), (err0, err1)
