@@ -124,3 +124,31 @@ def test_batch_pins_its_plans(torch):
     p.autotune()
     for e in ents:
         e[0].close()
+
+
+def test_batch_mixes_volumes_and_bscans(torch):
+    """A volume entry (2-D lateral transform) beside B-scans in one graph:
+    each equals its plan's isam_solve, the volume also the oracle's FISTA."""
+    from paper_1905_06058_gb300.isam import Batch, Plan
+    ents = entries(torch, seed0=90)[:2]
+    wl = I.small_bscan(nx=16, ny=24, nk=64, nz=64, na=0.12, seed=95, n_points=8)
+    op = O.IsamOracle(wl.geom, "nufft")
+    s = I.add_noise(op.forward(wl.eta), 30.0, np.random.default_rng(95))
+    plan = Plan(wl.geom)
+    kw = dict(lambda_rel=0.03, max_iter=15, L=plan.lipschitz())
+    sd = torch.from_numpy(s.astype(np.float32)).cuda()
+    res = torch.empty(plan.image_shape, dtype=torch.complex64, device="cuda")
+    items = [(plan, sd, res, kw)] + [(p, d, r, k) for p, d, r, k, *_ in ents]
+    b = Batch(items)
+    infos = b.run()
+    for (p, d, r, k), info in zip(items, infos):
+        assert info["status"] == 0 and info["iterations"] == k["max_iter"]
+        ref, _ = p.solve(d, **k)
+        assert rel(r.cpu().numpy(), ref.cpu().numpy()) < 1e-5
+    lam = O.lambda_from_data(op.adjoint, s, kw["lambda_rel"])
+    ref = O.fista(op.forward, op.adjoint, s, lam, kw["L"], max_iter=kw["max_iter"],
+                  shape=op.image_shape)
+    assert rel(res.cpu().numpy(), ref.eta) < 1e-3
+    b.close()
+    for p, *_ in items:
+        p.close()
