@@ -194,3 +194,46 @@ def test_full_bscan_adjoint_sampled_rows(torch):
     a_ref = np.fft.ifft(G, axis=0, norm="ortho")
     # exact-definition reference: NUFFT (J = 6) approximation plus FP32 rounding
     assert rel(a[:, rows], a_ref) < 3e-5
+
+
+# --------------------------------------------------------------------------
+# Full-size volume (256 x 256 A-scans x 2048 samples, 2-D lateral transform,
+# the benchmarked volume launch): sampled k planes of A eta and sampled depth
+# planes of A^H y, each computed by the oracle one plane at a time.
+# --------------------------------------------------------------------------
+
+@pytest.mark.slow
+def test_full_volume_forward_adjoint_sampled(torch):
+    wl = I.config3(dtype=np.complex64)
+    g = wl.geom
+    ref = O.IsamOracle(g, "nufft")
+    gr = ref.grid
+    plan = plan_for(g)
+    # forward: S(q, k) at six k for every (qy, qx) column, then the 2-D lateral IFFT
+    s = plan.forward(to_dev(torch, wl.eta, "fp32", True))
+    ks = np.array([0, 1, 777, 1024, 2046, 2047])
+    s = s[:, :, torch.from_numpy(ks).cuda()].cpu().numpy()
+    eta_hat = O.lateral_fft(wl.eta.astype(np.complex128))
+    S = np.zeros((g.ny, g.nx, ks.size), complex)
+    for iy in range(g.ny):
+        for ix in range(g.nx):
+            S[iy, ix] = O.nufft_forward_column(eta_hat[iy, ix] / math.sqrt(gr.nz),
+                                               ref.p[iy, ix, ks], ref.interp)
+    del eta_hat
+    S *= ref.phase[:, :, ks] * ref.prop[:, :, ks]
+    assert rel(s, O.lateral_ifft(S).real) < 1e-5
+    # adjoint: the exact sum over k of R(q, k) e^{+j beta z} at six depths
+    y = I.random_spectra(ref.spec_shape, 4).astype(np.float32)
+    a = plan.adjoint(to_dev(torch, y, "fp32", False))
+    rows = np.array([0, 5, 1023, 1024, 1500, 2047])
+    a = a[:, :, torch.from_numpy(rows).cuda()].cpu().numpy()
+    plan.close()
+    R = O.lateral_fft(y.astype(np.float64).astype(complex)) * np.conj(ref.phase) * ref.prop
+    G = np.zeros((g.ny, g.nx, rows.size), complex)
+    for i, r in enumerate(rows):
+        for iy in range(0, g.ny, 32):
+            E = np.exp(1j * gr.z[r] * ref.beta[iy:iy + 32])
+            G[iy:iy + 32, :, i] = np.einsum("yxk,yxk->yx", R[iy:iy + 32], E)
+    G /= math.sqrt(gr.nz)
+    # exact-definition reference: NUFFT (J = 6) approximation plus FP32 rounding
+    assert rel(a, O.lateral_ifft(G)) < 3e-5
