@@ -299,4 +299,95 @@ __device__ __forceinline__ void fft_smem(E* buf, int stride, int col, int b, int
   }
 }
 
+// ---------------------------------------------------------------------------
+// Compile-time-length Stockham transforms of column `col` at a compile-time
+// stride (element of logical row r at buf[prow(r) * STRIDE + col]), thread b
+// < L/8 active on every call.  With L, the stride and the pass span Ns
+// constant, the rows a thread reads (j + r L/R) and writes (base + r Ns) lie
+// at constant distances in the padded layout whenever the distance is a
+// multiple of 8 rows, so each pass computes one padded base row for its reads
+// and one for its writes and every access is a fixed offset from them.  Same
+// arithmetic, in the same order, as stockham_pass / fft_smem.
+// ---------------------------------------------------------------------------
+
+// padded row of logical row r0 + r * STEP, given p0 = prow(r0): with STEP a
+// compile-time multiple of 8 it is a fixed offset from p0
+template <int STEP>
+__device__ __forceinline__ int prow_at(int r0, int p0, int r) {
+  if constexpr (STEP % 8 == 0) return p0 + r * (STEP + STEP / 8);
+  else return prow(r0 + r * STEP);
+}
+
+template <int SIGN, int R, typename T, typename E>
+__device__ __forceinline__ void twiddle_powers(E* a, cplx<T> w1) {
+  if (SIGN > 0) w1.y = -w1.y;
+  cplx<T> w = w1;
+  a[1] = emul(a[1], w);
+#pragma unroll
+  for (int r = 2; r < R; ++r) {
+    w = cmul(w, w1);
+    a[r] = emul(a[r], w);
+  }
+}
+
+template <int SIGN, int R, int L, int NS, bool HALF_ZERO, int STRIDE, typename T, typename E>
+__device__ __forceinline__ void stockham_pass_ct(E* buf, int col, int b, const cplx<T>* tw) {
+  constexpr int NB = 8 / R;          // butterflies per thread
+  constexpr int LR = L / R;
+  constexpr int L8 = L / 8;
+  E v[8];
+#pragma unroll
+  for (int u = 0; u < NB; ++u) {
+    const int j = b + u * L8;
+    const int p0 = prow(j);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (HALF_ZERO && R == 8 && r >= 2 && r <= 5) v[u * R + r] = E{};
+      else v[u * R + r] = buf[prow_at<LR>(j, p0, r) * STRIDE + col];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < NB; ++u) {
+    const int j = b + u * L8;
+    const int k = j & (NS - 1);
+    E* a = v + u * R;
+    if (NS > 1) twiddle_powers<SIGN, R, T>(a, tw[k]);
+    if (R == 8) dft8<SIGN, HALF_ZERO>(a);
+    else if (R == 4) dft4<SIGN>(a[0], a[1], a[2], a[3]);
+    else dft2<SIGN>(a[0], a[1]);
+    const int base = (j - k) * R + k;
+    const int q0 = prow(base);
+#pragma unroll
+    for (int r = 0; r < R; ++r) buf[prow_at<NS>(base, q0, r) * STRIDE + col] = a[r];
+  }
+  __syncthreads();
+}
+
+template <int SIGN, bool HALF_ZERO, int L, int NS, int STRIDE, typename T, typename E>
+__device__ __forceinline__ void fft_passes_ct(E* buf, int col, int b, const cplx<T>* tw) {
+  if constexpr (NS * 8 <= L) {
+    stockham_pass_ct<SIGN, 8, L, NS, HALF_ZERO && NS == 1, STRIDE, T>(buf, col, b, tw);
+    fft_passes_ct<SIGN, HALF_ZERO, L, NS * 8, STRIDE, T>(buf, col, b, tw + (NS > 1 ? NS : 0));
+  } else if constexpr (NS * 4 == L) {
+    stockham_pass_ct<SIGN, 4, L, NS, false, STRIDE, T>(buf, col, b, tw);
+  } else if constexpr (NS * 2 == L) {
+    stockham_pass_ct<SIGN, 2, L, NS, false, STRIDE, T>(buf, col, b, tw);
+  }
+}
+
+// fft_smem for L = 2^LOGL (LOGL >= 3) and the stride known at compile time;
+// thread b < L/8 transforms column col.  Ends with a barrier.
+template <int SIGN, bool HALF_ZERO, int LOGL, int STRIDE, typename T, typename E>
+__device__ __forceinline__ void fft_cols_ct(E* buf, int col, int b, const cplx<T>* tw) {
+  static_assert(LOGL >= 3, "compile-time transforms start at L = 8");
+  fft_passes_ct<SIGN, HALF_ZERO, (1 << LOGL), 1, STRIDE, T>(buf, col, b, tw);
+}
+
+// one column at stride 1 (the axial kernels: every thread of a block of L/8)
+template <int SIGN, bool HALF_ZERO, int LOGL, typename T, typename E>
+__device__ __forceinline__ void fft_smem_ct(E* buf, int b, const cplx<T>* tw) {
+  fft_cols_ct<SIGN, HALF_ZERO, LOGL, 1, T>(buf, 0, b, tw);
+}
+
 }  // namespace isam

@@ -178,17 +178,39 @@ __device__ __forceinline__ cplx<T>* twiddle_table(unsigned char* raw, int K) {
   return reinterpret_cast<cplx<T>*>(raw + size_t(padded_rows(K)) * sizeof(cpair<T>));
 }
 
+// K-point transforms of the block's column pair: the compile-time-length
+// Stockham form when LOGK > 0 (K = 2^LOGK, the sizes the kernels are
+// instantiated for), else the runtime-length one.  Each ends with a barrier.
+template <int LOGK, typename T>
+__device__ __forceinline__ void axial_fft_fwd(cpair<T>* Y, int K, int logK, const cplx<T>* tw) {
+  if constexpr (LOGK > 0) fft_smem_ct<+1, true, LOGK, T>(Y, threadIdx.x, tw);
+  else fft_smem<+1, true, T>(Y, 1, 0, threadIdx.x, K, logK, tw, true);
+}
+template <int LOGK, typename T>
+__device__ __forceinline__ void axial_fft_inv(cpair<T>* Y, int K, int logK, const cplx<T>* tw) {
+  if constexpr (LOGK > 0) fft_smem_ct<-1, false, LOGK, T>(Y, threadIdx.x, tw);
+  else fft_smem<-1, false, T>(Y, 1, 0, threadIdx.x, K, logK, tw, true);
+}
+
+// K and the block size K/8, as compile-time constants when LOGK > 0
+template <int LOGK> __device__ __forceinline__ int axial_K(const StoltConst& sc) {
+  return LOGK > 0 ? (1 << LOGK) : sc.K;
+}
+template <int LOGK> __device__ __forceinline__ int axial_threads() {
+  return LOGK > 0 ? (1 << LOGK) / 8 : int(blockDim.x);
+}
+
 // Y (padded rows) = scaled columns c1 (a) and c2 (b), zero-padded to K, then
 // the K-point e^{+} DFT.  The padding rows [nz/2, K - nz/2) are never stored:
 // the first FFT pass knows them to be zero.  Ends with a barrier.
-template <typename T>
+template <typename T, int LOGK>
 __device__ __forceinline__ void load_and_fft(const AxArgs<T>& A, cpair<T>* Y, const cplx<T>* tw,
                                              int c1, int c2, bool two) {
   using C = cplx<T>;
   using V = cpair<T>;
   const StoltConst& sc = A.sc;
-  const int K = sc.K, nz = sc.nz;
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int K = axial_K<LOGK>(sc), nz = K / 2;
+  const int tid = threadIdx.x, nt = axial_threads<LOGK>();
   const C* x1 = A.in + size_t(c1) * nz;
   const C* x2 = A.in + size_t(c2) * nz;
   // nz = 4 * blockDim: four samples per thread, loads issued before use
@@ -207,7 +229,7 @@ __device__ __forceinline__ void load_and_fft(const AxArgs<T>& A, cpair<T>* Y, co
     Y[prow(p)] = escale(v[i], __ldg(A.tab.scale + n));
   }
   __syncthreads();
-  fft_smem<+1, true, T>(Y, 1, 0, tid, K, sc.logK, tw, true);
+  axial_fft_fwd<LOGK, T>(Y, K, sc.logK, tw);
 }
 
 // forward interpolation of both columns at sample j (before the phase)
@@ -252,10 +274,10 @@ template <typename T> struct Sample {
 // chunk the J-bin neighbourhoods span fewer than K bins, so they never meet
 // again after the wrap mod K.  Returns the number of chunks.
 template <typename T, int J>
-__device__ __forceinline__ int prepare_scatter(cpair<T>* Y, int K, Sample<T>* sm, int* lo,
+__device__ __forceinline__ int prepare_scatter(cpair<T>* Y, int K, int nt, Sample<T>* sm, int* lo,
                                                int* hi) {
   const cpair<T> zero = {mk<T>(0, 0), mk<T>(0, 0)};
-  for (int i = threadIdx.x; i < K; i += blockDim.x) Y[prow(i)] = zero;
+  for (int i = threadIdx.x; i < K; i += nt) Y[prow(i)] = zero;
   int l = INT_MAX, h = INT_MIN;
 #pragma unroll
   for (int rho = 0; rho < NRES; ++rho)
@@ -285,10 +307,9 @@ __device__ __forceinline__ int prepare_scatter(cpair<T>* Y, int K, Sample<T>* sm
 // Y must be zero; every thread adds its samples' J contributions, residue
 // class by residue class and chunk by chunk (see the comment above NRES).
 template <typename T, int J>
-__device__ __forceinline__ void scatter_samples(const AxArgs<T>& A, cpair<T>* Y,
+__device__ __forceinline__ void scatter_samples(const AxArgs<T>& A, cpair<T>* Y, int K,
                                                 const Sample<T>* sm, int nchunks) {
   using V = cpair<T>;
-  const int K = A.sc.K;
   for (int ch = 0; ch < nchunks; ++ch) {
 #pragma unroll
     for (int rho = 0; rho < NRES; ++rho) {
@@ -314,14 +335,14 @@ __device__ __forceinline__ void scatter_samples(const AxArgs<T>& A, cpair<T>* Y,
 }
 
 // Y (after the e^{-} DFT): truncate to the nz samples, scale, store columns.
-template <typename T>
+template <typename T, int LOGK>
 __device__ __forceinline__ void store_columns(const AxArgs<T>& A, const cpair<T>* Y, int c1,
                                               int c2, bool two) {
   using C = cplx<T>;
-  const int K = A.sc.K, nz = A.sc.nz;
+  const int K = axial_K<LOGK>(A.sc), nz = K / 2, nt = axial_threads<LOGK>();
   C* o1 = A.out + size_t(c1) * nz;
   C* o2 = A.out + size_t(c2) * nz;
-  for (int n = threadIdx.x; n < nz; n += blockDim.x) {
+  for (int n = threadIdx.x; n < nz; n += nt) {
     int p = n - nz / 2;
     if (p < 0) p += K;
     const T s = __ldg(A.tab.scale + n);
@@ -331,25 +352,25 @@ __device__ __forceinline__ void store_columns(const AxArgs<T>& A, const cpair<T>
   }
 }
 
-template <typename T, int J>
+template <typename T, int J, int LOGK>
 __global__ void __launch_bounds__(512) k_ax_fwd(const __grid_constant__ AxArgs<T> A) {
   using C = cplx<T>;
   using V = cpair<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const StoltConst& sc = A.sc;
-  const int K = sc.K, nk = sc.nk;
+  const int K = axial_K<LOGK>(sc), nk = sc.nk;
   V* Y = reinterpret_cast<V*>(smem_raw);
   cplx<T>* tw = twiddle_table<T>(smem_raw, K);
   int c1, c2, mx, my;
   pair_columns(A, c1, c2, mx, my);
   const bool two = c2 != c1;
   build_twiddles<T>(tw, K, sc.logK);
-  load_and_fft(A, Y, tw, c1, c2, two);
+  load_and_fft<T, LOGK>(A, Y, tw, c1, c2, two);
 
   const Positions<T> pos(A, mx, my);
   C* o1 = A.out + size_t(c1) * nk;
   C* o2 = A.out + size_t(c2) * nk;
-  for (int j = threadIdx.x; j < nk; j += blockDim.x) {
+  for (int j = threadIdx.x; j < nk; j += axial_threads<LOGK>()) {
     int mfl;
     T frac;
     C ph;
@@ -366,13 +387,13 @@ __global__ void __launch_bounds__(512) k_ax_fwd(const __grid_constant__ AxArgs<T
   }
 }
 
-template <typename T, int J>
+template <typename T, int J, int LOGK>
 __global__ void __launch_bounds__(512, 2) k_ax_adj(const __grid_constant__ AxArgs<T> A) {
   using C = cplx<T>;
   using V = cpair<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const StoltConst& sc = A.sc;
-  const int K = sc.K, nk = sc.nk;
+  const int K = axial_K<LOGK>(sc), nk = sc.nk;
   V* Y = reinterpret_cast<V*>(smem_raw);
   cplx<T>* tw = twiddle_table<T>(smem_raw, K);
   __shared__ int ch_lo, ch_hi;
@@ -401,10 +422,10 @@ __global__ void __launch_bounds__(512, 2) k_ax_adj(const __grid_constant__ AxArg
       sm[rho].chunk = 0;
     }
   }
-  const int nch = prepare_scatter<T, J>(Y, K, sm, &ch_lo, &ch_hi);
-  scatter_samples<T, J>(A, Y, sm, nch);
-  fft_smem<-1, false, T>(Y, 1, 0, tid, K, sc.logK, tw, true);
-  store_columns(A, Y, c1, c2, two);
+  const int nch = prepare_scatter<T, J>(Y, K, axial_threads<LOGK>(), sm, &ch_lo, &ch_hi);
+  scatter_samples<T, J>(A, Y, K, sm, nch);
+  axial_fft_inv<LOGK, T>(Y, K, sc.logK, tw);
+  store_columns<T, LOGK>(A, Y, c1, c2, two);
 }
 
 // Forward model, data residual and adjoint of one column pair in one pass
@@ -414,18 +435,18 @@ __global__ void __launch_bounds__(512, 2) k_ax_adj(const __grid_constant__ AxArg
 // because F(Re v)(q) = (F v(q) + conj(F v(-q))) / 2 and q, -q are the two
 // columns of the pair; then G = N'(conj(phase) R).  F s_d is Hermitian, so
 // only its c1 column is read.  Optionally writes ||R||^2 of the pair.
-template <typename T, int J>
+template <typename T, int J, int LOGK>
 __global__ void __launch_bounds__(512, 2) k_ax_fused(const __grid_constant__ AxArgs<T> A) {
   using C = cplx<T>;
   using V = cpair<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const StoltConst& sc = A.sc;
-  const int K = sc.K, nk = sc.nk;
+  const int K = axial_K<LOGK>(sc), nk = sc.nk;
   V* Y = reinterpret_cast<V*>(smem_raw);
   cplx<T>* tw = twiddle_table<T>(smem_raw, K);
   __shared__ int ch_lo, ch_hi;
   __shared__ double red[16];
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int tid = threadIdx.x, nt = axial_threads<LOGK>();
   int c1, c2, mx, my;
   pair_columns(A, c1, c2, mx, my);
   const bool two = c2 != c1;
@@ -444,7 +465,7 @@ __global__ void __launch_bounds__(512, 2) k_ax_fused(const __grid_constant__ AxA
     const int j = NRES * tid + rho;
     dqv[rho] = j < nk ? d1[j] : mk<T>(0, 0);
   }
-  load_and_fft(A, Y, tw, c1, c2, two);
+  load_and_fft<T, LOGK>(A, Y, tw, c1, c2, two);
 
   const Positions<T> pos(A, mx, my);
   Sample<T> sm[NRES];
@@ -490,10 +511,10 @@ __global__ void __launch_bounds__(512, 2) k_ax_fused(const __grid_constant__ AxA
     for (int w = 0; w < (nt >> 5); ++w) t += red[w];
     A.partial[blockIdx.x] = t;
   }
-  const int nch = prepare_scatter<T, J>(Y, K, sm, &ch_lo, &ch_hi);
-  scatter_samples<T, J>(A, Y, sm, nch);
-  fft_smem<-1, false, T>(Y, 1, 0, tid, K, sc.logK, tw, true);
-  store_columns(A, Y, c1, c2, two);
+  const int nch = prepare_scatter<T, J>(Y, K, axial_threads<LOGK>(), sm, &ch_lo, &ch_hi);
+  scatter_samples<T, J>(A, Y, K, sm, nch);
+  axial_fft_inv<LOGK, T>(Y, K, sc.logK, tw);
+  store_columns<T, LOGK>(A, Y, c1, c2, two);
 }
 
 // One thread per (|q| class, k_j): the same evaluation the kernels do on the fly.
@@ -541,19 +562,19 @@ template size_t ax_smem_bytes<double>(int, int, bool);
 
 enum { AX_FWD = 0, AX_ADJ = 1, AX_FUSED = 2 };
 
-template <typename T, int J>
-static cudaError_t launch_ax_J(const AxArgs<T>& a, int npairs, cudaStream_t s, int kind) {
+template <typename T, int J, int LOGK>
+static cudaError_t launch_ax_JK(const AxArgs<T>& a, int npairs, cudaStream_t s, int kind) {
   const int K = a.sc.K;
   const int threads = K / 8;
   const size_t sm = ax_smem_bytes<T>(K, a.sc.nk, kind != AX_FWD);
   if (kind == AX_ADJ) {
-    cudaFuncSetAttribute(k_ax_adj<T, J>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-    k_ax_adj<T, J><<<npairs, threads, sm, s>>>(a);
+    cudaFuncSetAttribute(k_ax_adj<T, J, LOGK>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    k_ax_adj<T, J, LOGK><<<npairs, threads, sm, s>>>(a);
   } else if (kind == AX_FWD) {
-    cudaFuncSetAttribute(k_ax_fwd<T, J>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-    k_ax_fwd<T, J><<<npairs, threads, sm, s>>>(a);
+    cudaFuncSetAttribute(k_ax_fwd<T, J, LOGK>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    k_ax_fwd<T, J, LOGK><<<npairs, threads, sm, s>>>(a);
   } else {
-    cudaFuncSetAttribute(k_ax_fused<T, J>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    cudaFuncSetAttribute(k_ax_fused<T, J, LOGK>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
     // programmatic dependent launch (see k_ax_fused's prologue)
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(npairs);
@@ -565,9 +586,19 @@ static cudaError_t launch_ax_J(const AxArgs<T>& a, int npairs, cudaStream_t s, i
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_ax_fused<T, J>, a);
+    return cudaLaunchKernelEx(&cfg, k_ax_fused<T, J, LOGK>, a);
   }
   return cudaGetLastError();
+}
+
+// K = 4096 and 2048 (nz = 2048, 1024) run the compile-time-length instances
+template <typename T, int J>
+static cudaError_t launch_ax_J(const AxArgs<T>& a, int npairs, cudaStream_t s, int kind) {
+  switch (a.sc.K) {
+    case 4096: return launch_ax_JK<T, J, 12>(a, npairs, s, kind);
+    case 2048: return launch_ax_JK<T, J, 11>(a, npairs, s, kind);
+  }
+  return launch_ax_JK<T, J, 0>(a, npairs, s, kind);
 }
 
 template <typename T>

@@ -13,6 +13,8 @@
 // with partial norms for the relative residual (Eq. 15).
 #include <math.h>
 
+#include <type_traits>
+
 #include "fft_smem.cuh"
 #include "internal.cuh"
 
@@ -63,7 +65,10 @@ template <typename T> struct rpair_t;
 template <> struct rpair_t<float> { using type = float2; };
 template <> struct rpair_t<double> { using type = double2; };
 
-template <typename T, int MODE>
+// LOGL > 0: the transforms are the compile-time-length ones for L = 2^LOGL at
+// the stride 2^LOGTP = TP (no radix-3 pass), with constant row offsets;
+// LOGL = 0: runtime-length transforms.  The tile indexing is the same.
+template <typename T, int MODE, int LOGL, int LOGTP>
 __global__ void __launch_bounds__(512, 2) k_lat(const __grid_constant__ LatArgs<T> a) {
   using C = cplx<T>;
   using V = cpair<T>;
@@ -71,12 +76,13 @@ __global__ void __launch_bounds__(512, 2) k_lat(const __grid_constant__ LatArgs<
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* buf = reinterpret_cast<V*>(smem_raw);
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int TP = a.TZ, L = a.L, logTP = a.logTZ;
+  constexpr bool CT = LOGL > 0;
+  const int TP = a.TZ, L = CT ? (1 << LOGL) : a.L, logTP = a.logTZ;
   cplx<T>* tw = reinterpret_cast<cplx<T>*>(buf + size_t(padded_rows(L)) * TP);
   // programmatic dependent launch: let the next kernel start its prologue,
   // build the twiddles, then wait for the previous kernel's results
   cudaTriggerProgrammaticLaunchCompletion();
-  build_twiddles<T>(tw, L, a.logL, a.r3);
+  build_twiddles<T>(tw, L, CT ? LOGL : a.logL, CT ? 0 : a.r3);
   cudaGridDependencySynchronize();
   const int col = tid & (TP - 1), b = tid >> logTP;
   const size_t M = size_t(a.M);
@@ -89,6 +95,13 @@ __global__ void __launch_bounds__(512, 2) k_lat(const __grid_constant__ LatArgs<
   const int ept = n_el / nt;
   auto gidx = [&](int e) { return base + size_t(e >> logTP) * M + 2 * (e & (TP - 1)); };
   auto sidx = [&](int e) { return prow(e >> logTP) * TP + (e & (TP - 1)); };
+  auto lat_fft = [&](auto sign) {
+    constexpr int SIGN = decltype(sign)::value;
+    if constexpr (CT) fft_cols_ct<SIGN, false, LOGL, (1 << LOGTP), T>(buf, col, b, tw);
+    else fft_smem<SIGN, false, T>(buf, TP, col, b, L, a.logL, tw, true, a.r3);
+  };
+  using FWD = std::integral_constant<int, -1>;
+  using INV = std::integral_constant<int, +1>;
 
   // load the tile: all global loads first, then the shared-memory stores
   {
@@ -117,10 +130,8 @@ __global__ void __launch_bounds__(512, 2) k_lat(const __grid_constant__ LatArgs<
   }
   __syncthreads();
 
-  if (MODE == LAT_C2C_FWD || MODE == LAT_R2C_FWD || MODE == LAT_EXTRAP_FWD)
-    fft_smem<-1, false, T>(buf, TP, col, b, L, a.logL, tw, true, a.r3);
-  else
-    fft_smem<+1, false, T>(buf, TP, col, b, L, a.logL, tw, true, a.r3);
+  if (MODE == LAT_C2C_FWD || MODE == LAT_R2C_FWD || MODE == LAT_EXTRAP_FWD) lat_fft(FWD{});
+  else lat_fft(INV{});
 
   const T nrm = a.norm;
   if (MODE == LAT_C2C_FWD || MODE == LAT_C2C_INV || MODE == LAT_R2C_FWD ||
@@ -216,7 +227,7 @@ __global__ void __launch_bounds__(512, 2) k_lat(const __grid_constant__ LatArgs<
   }
   if (bad) atomicOr(a.flag, 1);
   __syncthreads();
-  fft_smem<-1, false, T>(buf, TP, col, b, L, a.logL, tw, true, a.r3);
+  lat_fft(FWD{});
   C* out = static_cast<C*>(a.out);
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
@@ -308,11 +319,12 @@ template <typename T> size_t lat_smem_bytes(int L, int TP) {
          size_t(twiddle_entries(L, lg, r3)) * sizeof(cplx<T>);
 }
 
-template <typename T, int MODE>
-static cudaError_t launch_lat_mode(const LatArgs<T>& a, cudaStream_t s) {
+template <typename T, int MODE, int LOGL, int LOGTP>
+static cudaError_t launch_lat_tile(const LatArgs<T>& a, cudaStream_t s) {
   const int threads = (a.L >= 8 ? a.L / 8 : 1) * a.TZ;
   const size_t sm = lat_smem_bytes<T>(a.L, a.TZ);
-  cudaFuncSetAttribute(k_lat<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+  auto* kern = k_lat<T, MODE, LOGL, LOGTP>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
   dim3 grid(a.M / (2 * a.TZ), a.B);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
@@ -324,7 +336,23 @@ static cudaError_t launch_lat_mode(const LatArgs<T>& a, cudaStream_t s) {
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_lat<T, MODE>, a);
+  return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+// The FP32 solve passes at the tiles of the 1024-wide B-scans (L = 1024, 4
+// pair-columns), the 512-wide ones and the 256 x 256 volumes (L = 512 or 256, 8
+// pair-columns) run compile-time-length transforms; every other case the
+// runtime-length ones.
+template <typename T, int MODE>
+static cudaError_t launch_lat_mode(const LatArgs<T>& a, cudaStream_t s) {
+  constexpr bool hot = std::is_same<T, float>::value &&
+                       (MODE == LAT_UPDATE || MODE == LAT_C2C_FWD || MODE == LAT_C2C_INV);
+  if constexpr (hot) {
+    if (!a.r3 && a.L == 1024 && a.TZ == 4) return launch_lat_tile<T, MODE, 10, 2>(a, s);
+    if (!a.r3 && a.L == 512 && a.TZ == 8) return launch_lat_tile<T, MODE, 9, 3>(a, s);
+    if (!a.r3 && a.L == 256 && a.TZ == 8) return launch_lat_tile<T, MODE, 8, 3>(a, s);
+  }
+  return launch_lat_tile<T, MODE, 0, 0>(a, s);
 }
 
 template <typename T> cudaError_t launch_lat(int mode, const LatArgs<T>& a, cudaStream_t s) {
