@@ -180,7 +180,8 @@ __device__ __forceinline__ cplx<T>* twiddle_table(unsigned char* raw, int K) {
 
 // K-point transforms of the block's column pair: the compile-time-length
 // Stockham form when LOGK > 0 (K = 2^LOGK, the sizes the kernels are
-// instantiated for), else the runtime-length one.  Each ends with a barrier.
+// instantiated for), else the runtime-length one.  The inverse's compile-time
+// form writes only the rows store_columns keeps.  Each ends with a barrier.
 template <int LOGK, typename T>
 __device__ __forceinline__ void axial_fft_fwd(cpair<T>* Y, int K, int logK, const cplx<T>* tw) {
   if constexpr (LOGK > 0) fft_smem_ct<+1, true, LOGK, T>(Y, threadIdx.x, tw);
@@ -188,7 +189,7 @@ __device__ __forceinline__ void axial_fft_fwd(cpair<T>* Y, int K, int logK, cons
 }
 template <int LOGK, typename T>
 __device__ __forceinline__ void axial_fft_inv(cpair<T>* Y, int K, int logK, const cplx<T>* tw) {
-  if constexpr (LOGK > 0) fft_smem_ct<-1, false, LOGK, T>(Y, threadIdx.x, tw);
+  if constexpr (LOGK > 0) fft_smem_ct<-1, false, LOGK, T, true>(Y, threadIdx.x, tw);
   else fft_smem<-1, false, T>(Y, 1, 0, threadIdx.x, K, logK, tw, true);
 }
 
