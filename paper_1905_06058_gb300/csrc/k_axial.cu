@@ -274,9 +274,17 @@ template <typename T> struct Sample {
 // every sample to a chunk of width K - J of unwrapped positions: within a
 // chunk the J-bin neighbourhoods span fewer than K bins, so they never meet
 // again after the wrap mod K.  Returns the number of chunks.
+//
+// warp_tail: there are two chunks and every chunk-1 sample belongs to the
+// block's last warp.  Stolt positions rise with j (samples below the
+// evanescent cut-off come first) and warp w owns samples
+// [32 NRES w, 32 NRES (w + 1)), so this holds when the last sample of the
+// warp before it, j* = NRES (nt - 32) - 1 (thread nt - 33), exists (j* < nk)
+// and is in chunk 0 or evanescent.  Its position goes through *tail
+// (INT_MAX: j* >= nk, INT_MIN: evanescent).
 template <typename T, int J>
-__device__ __forceinline__ int prepare_scatter(cpair<T>* Y, int K, int nt, Sample<T>* sm, int* lo,
-                                               int* hi) {
+__device__ __forceinline__ int prepare_scatter(cpair<T>* Y, int K, int nt, int nk, Sample<T>* sm,
+                                               int* lo, int* hi, int* tail, bool& warp_tail) {
   const cpair<T> zero = {mk<T>(0, 0), mk<T>(0, 0)};
   for (int i = threadIdx.x; i < K; i += nt) Y[prow(i)] = zero;
   int l = INT_MAX, h = INT_MIN;
@@ -290,8 +298,12 @@ __device__ __forceinline__ int prepare_scatter(cpair<T>* Y, int K, int nt, Sampl
     atomicMin(lo, l);
     atomicMax(hi, h);
   }
+  if (int(threadIdx.x) == nt - 33)
+    *tail = NRES * (nt - 32) - 1 >= nk ? INT_MAX
+            : (sm[NRES - 1].chunk != INT_MIN ? sm[NRES - 1].mfl : INT_MIN);
   __syncthreads();
   const int base = *lo, width = K - J;
+  warp_tail = false;
   if (base == INT_MAX) return 0;
 #pragma unroll
   for (int rho = 0; rho < NRES; ++rho)
@@ -302,36 +314,57 @@ __device__ __forceinline__ int prepare_scatter(cpair<T>* Y, int K, int nt, Sampl
     }
   int n = 1;
   for (int d = *hi - base; d >= width; d -= width) ++n;
+  const int t = *tail;
+  warp_tail = n == 2 && nt >= 64 && t != INT_MAX && (t == INT_MIN || t - base < width);
   return n;
 }
 
-// Y must be zero; every thread adds its samples' J contributions, residue
-// class by residue class and chunk by chunk (see the comment above NRES).
+// the J contributions of one sample
 template <typename T, int J>
-__device__ __forceinline__ void scatter_samples(const AxArgs<T>& A, cpair<T>* Y, int K,
-                                                const Sample<T>* sm, int nchunks) {
+__device__ __forceinline__ void add_sample(const AxArgs<T>& A, cpair<T>* Y, int K,
+                                           const Sample<T>& sm) {
   using V = cpair<T>;
-  for (int ch = 0; ch < nchunks; ++ch) {
+  T c[J];
+  coefficients<T, J>(A.poly, sm.frac, c);
+  const int m0 = sm.mfl - J / 2 + 1;
+  const V v = sm.val;
+#pragma unroll
+  for (int l = 0; l < J; ++l) {
+    const int bi = prow((m0 + l) & (K - 1));
+    V y = Y[bi];
+    y.a.x = fma(c[l], v.a.x, y.a.x);
+    y.a.y = fma(c[l], v.a.y, y.a.y);
+    y.b.x = fma(c[l], v.b.x, y.b.x);
+    y.b.y = fma(c[l], v.b.y, y.b.y);
+    Y[bi] = y;
+  }
+}
+
+// Y must be zero; every thread adds its samples' J contributions, residue
+// class by residue class and chunk by chunk (see the comment above NRES),
+// each phase closed by a block barrier.  With warp_tail the last chunk's
+// phases involve the last warp only and are closed by warp barriers, then one
+// block barrier: the same phases in the same order, so the same sums.
+template <typename T, int J>
+__device__ __forceinline__ void scatter_samples(const AxArgs<T>& A, cpair<T>* Y, int K, int nt,
+                                                const Sample<T>* sm, int nchunks, bool warp_tail) {
+  const int block_chunks = warp_tail ? 1 : nchunks;
+  for (int ch = 0; ch < block_chunks; ++ch) {
 #pragma unroll
     for (int rho = 0; rho < NRES; ++rho) {
-      if (sm[rho].chunk == ch) {
-        T c[J];
-        coefficients<T, J>(A.poly, sm[rho].frac, c);
-        const int m0 = sm[rho].mfl - J / 2 + 1;
-        const V v = sm[rho].val;
-#pragma unroll
-        for (int l = 0; l < J; ++l) {
-          const int bi = prow((m0 + l) & (K - 1));
-          V y = Y[bi];
-          y.a.x = fma(c[l], v.a.x, y.a.x);
-          y.a.y = fma(c[l], v.a.y, y.a.y);
-          y.b.x = fma(c[l], v.b.x, y.b.x);
-          y.b.y = fma(c[l], v.b.y, y.b.y);
-          Y[bi] = y;
-        }
-      }
+      if (sm[rho].chunk == ch) add_sample<T, J>(A, Y, K, sm[rho]);
       __syncthreads();
     }
+  }
+  if (warp_tail) {
+    if ((int(threadIdx.x) >> 5) == (nt >> 5) - 1) {
+#pragma unroll
+      for (int rho = 0; rho < NRES; ++rho) {
+        if (sm[rho].chunk == 1) add_sample<T, J>(A, Y, K, sm[rho]);
+        __syncwarp();
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -397,8 +430,8 @@ __global__ void __launch_bounds__(512, 2) k_ax_adj(const __grid_constant__ AxArg
   const int K = axial_K<LOGK>(sc), nk = sc.nk;
   V* Y = reinterpret_cast<V*>(smem_raw);
   cplx<T>* tw = twiddle_table<T>(smem_raw, K);
-  __shared__ int ch_lo, ch_hi;
-  const int tid = threadIdx.x;
+  __shared__ int ch_lo, ch_hi, ch_tail;
+  const int tid = threadIdx.x, nt = axial_threads<LOGK>();
   int c1, c2, mx, my;
   pair_columns(A, c1, c2, mx, my);
   const bool two = c2 != c1;
@@ -423,8 +456,9 @@ __global__ void __launch_bounds__(512, 2) k_ax_adj(const __grid_constant__ AxArg
       sm[rho].chunk = 0;
     }
   }
-  const int nch = prepare_scatter<T, J>(Y, K, axial_threads<LOGK>(), sm, &ch_lo, &ch_hi);
-  scatter_samples<T, J>(A, Y, K, sm, nch);
+  bool warp_tail;
+  const int nch = prepare_scatter<T, J>(Y, K, nt, nk, sm, &ch_lo, &ch_hi, &ch_tail, warp_tail);
+  scatter_samples<T, J>(A, Y, K, nt, sm, nch, warp_tail);
   axial_fft_inv<LOGK, T>(Y, K, sc.logK, tw);
   store_columns<T, LOGK>(A, Y, c1, c2, two);
 }
@@ -445,7 +479,7 @@ __global__ void __launch_bounds__(512, 2) k_ax_fused(const __grid_constant__ AxA
   const int K = axial_K<LOGK>(sc), nk = sc.nk;
   V* Y = reinterpret_cast<V*>(smem_raw);
   cplx<T>* tw = twiddle_table<T>(smem_raw, K);
-  __shared__ int ch_lo, ch_hi;
+  __shared__ int ch_lo, ch_hi, ch_tail;
   __shared__ double red[16];
   const int tid = threadIdx.x, nt = axial_threads<LOGK>();
   int c1, c2, mx, my;
@@ -512,8 +546,9 @@ __global__ void __launch_bounds__(512, 2) k_ax_fused(const __grid_constant__ AxA
     for (int w = 0; w < (nt >> 5); ++w) t += red[w];
     A.partial[blockIdx.x] = t;
   }
-  const int nch = prepare_scatter<T, J>(Y, K, axial_threads<LOGK>(), sm, &ch_lo, &ch_hi);
-  scatter_samples<T, J>(A, Y, K, sm, nch);
+  bool warp_tail;
+  const int nch = prepare_scatter<T, J>(Y, K, nt, nk, sm, &ch_lo, &ch_hi, &ch_tail, warp_tail);
+  scatter_samples<T, J>(A, Y, K, nt, sm, nch, warp_tail);
   axial_fft_inv<LOGK, T>(Y, K, sc.logK, tw);
   store_columns<T, LOGK>(A, Y, c1, c2, two);
 }
