@@ -370,18 +370,61 @@ __device__ __forceinline__ void stockham_pass_ct(E* buf, int col, int b, const c
   __syncthreads();
 }
 
-template <int SIGN, bool HALF_ZERO, bool TRUNC, int L, int NS, int STRIDE, typename T, typename E>
+// The passes of span NS and up (tw: the segment of span NS).  SKIP_LAST:
+// stop before the last pass (last_pass_regs_ct takes it).
+template <int SIGN, bool HALF_ZERO, bool TRUNC, int L, int NS, int STRIDE, typename T,
+          bool SKIP_LAST = false, typename E>
 __device__ __forceinline__ void fft_passes_ct(E* buf, int col, int b, const cplx<T>* tw) {
   if constexpr (NS * 8 <= L) {
     constexpr bool last = NS * 8 == L;
-    stockham_pass_ct<SIGN, 8, L, NS, HALF_ZERO && NS == 1, STRIDE, TRUNC && last, T>(buf, col, b,
-                                                                                     tw);
-    fft_passes_ct<SIGN, HALF_ZERO, TRUNC, L, NS * 8, STRIDE, T>(buf, col, b,
-                                                                tw + (NS > 1 ? NS : 0));
-  } else if constexpr (NS * 4 == L) {
+    if constexpr (!(last && SKIP_LAST))
+      stockham_pass_ct<SIGN, 8, L, NS, HALF_ZERO && NS == 1, STRIDE, TRUNC && last, T>(buf, col, b,
+                                                                                       tw);
+    fft_passes_ct<SIGN, HALF_ZERO, TRUNC, L, NS * 8, STRIDE, T, SKIP_LAST>(
+        buf, col, b, tw + (NS > 1 ? NS : 0));
+  } else if constexpr (NS * 4 == L && !SKIP_LAST) {
     stockham_pass_ct<SIGN, 4, L, NS, false, STRIDE, TRUNC, T>(buf, col, b, tw);
-  } else if constexpr (NS * 2 == L) {
+  } else if constexpr (NS * 2 == L && !SKIP_LAST) {
     stockham_pass_ct<SIGN, 2, L, NS, false, STRIDE, TRUNC, T>(buf, col, b, tw);
+  }
+}
+
+// Offset in the twiddle table of the segment of the pass with span ns (a
+// power of 8): the segments of the spans 8, 64, ... below it come first.
+__host__ __device__ constexpr int tw_offset(int ns) {
+  int o = 0;
+  for (int s = 8; s < ns; s *= 8) o += s;
+  return o;
+}
+
+// Register end of a compile-time transform.  Thread b owns the rows
+// b + i L/8, i < 8, of its column: in the last pass (span L/R) its butterflies
+// j = b + u L/8 read and write rows j + r L/R = b + (u + r 8/R) L/8, so the
+// last pass can hand its outputs to global stores without a shared-memory
+// round trip.
+//
+// last_pass_regs_ct: butterfly by butterfly, reads the last pass's inputs
+// (the previous pass must have ended with a barrier), computes them and hands
+// output row b + i L/8 to emit(i, value); writes no shared memory.
+template <int SIGN, int LOGL, int STRIDE, typename T, typename E, typename Emit>
+__device__ __forceinline__ void last_pass_regs_ct(const E* buf, int col, int b,
+                                                  const cplx<T>* tw_table, Emit emit) {
+  constexpr int L = 1 << LOGL, n8 = LOGL / 3, rem = LOGL - 3 * (LOGL / 3);
+  constexpr int R = rem == 0 ? 8 : (1 << rem);
+  constexpr int NS = L / R, NB = 8 / R, L8 = L / 8;
+  const cplx<T>* tw = tw_table + tw_offset(rem == 0 ? (1 << (3 * (n8 - 1))) : (1 << (3 * n8)));
+  const int p0 = prow(b);
+#pragma unroll
+  for (int u = 0; u < NB; ++u) {
+    E a[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) a[r] = buf[prow_at<L8>(b, p0, u + r * NB) * STRIDE + col];
+    if (NS > 1) twiddle_powers<SIGN, R, T>(a, tw[(b + u * L8) & (NS - 1)]);
+    if (R == 8) dft8<SIGN>(a);
+    else if (R == 4) dft4<SIGN>(a[0], a[1], a[2], a[3]);
+    else dft2<SIGN>(a[0], a[1]);
+#pragma unroll
+    for (int r = 0; r < R; ++r) emit(u + r * NB, a[r]);
   }
 }
 

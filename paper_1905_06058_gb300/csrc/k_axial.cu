@@ -386,6 +386,35 @@ __device__ __forceinline__ void store_columns(const AxArgs<T>& A, const cpair<T>
   }
 }
 
+// The inverse transform of Y and store_columns.  Compile-time K: the last
+// pass runs in registers and writes the kept rows straight to the columns
+// (the rows thread b's last-pass butterfly produces, b + i K/8, are rows it
+// stores: natural row p goes to sample n = p + nz/2 for p < nz/2 and
+// p - (K - nz/2) for p >= K - nz/2, nz = K/2; the others are dropped).
+template <typename T, int LOGK>
+__device__ __forceinline__ void inverse_and_store(const AxArgs<T>& A, cpair<T>* Y,
+                                                  const cplx<T>* tw, int c1, int c2, bool two) {
+  if constexpr (LOGK > 0) {
+    using C = cplx<T>;
+    constexpr int K = 1 << LOGK, nz = K / 2, K8 = K / 8;
+    const int b = threadIdx.x;
+    fft_passes_ct<-1, false, false, K, 1, 1, T, true>(Y, 0, b, tw);
+    C* o1 = A.out + size_t(c1) * nz;
+    C* o2 = A.out + size_t(c2) * nz;
+    last_pass_regs_ct<-1, LOGK, 1, T>(Y, 0, b, tw, [&](int i, const cpair<T>& y) {
+      const int p = b + i * K8;
+      if (i * K8 >= K / 4 && (i + 1) * K8 <= 3 * K / 4) return;   // rows [K/4, 3K/4)
+      const int n = p < K / 4 ? p + nz / 2 : p - (K - nz / 2);
+      const T s = __ldg(A.tab.scale + n);
+      o1[n] = cscale(y.a, s);
+      if (two) o2[n] = cscale(y.b, s);
+    });
+  } else {
+    axial_fft_inv<LOGK, T>(Y, A.sc.K, A.sc.logK, tw);
+    store_columns<T, LOGK>(A, Y, c1, c2, two);
+  }
+}
+
 template <typename T, int J, int LOGK>
 __global__ void __launch_bounds__(512) k_ax_fwd(const __grid_constant__ AxArgs<T> A) {
   using C = cplx<T>;
@@ -459,8 +488,7 @@ __global__ void __launch_bounds__(512, 2) k_ax_adj(const __grid_constant__ AxArg
   bool warp_tail;
   const int nch = prepare_scatter<T, J>(Y, K, nt, nk, sm, &ch_lo, &ch_hi, &ch_tail, warp_tail);
   scatter_samples<T, J>(A, Y, K, nt, sm, nch, warp_tail);
-  axial_fft_inv<LOGK, T>(Y, K, sc.logK, tw);
-  store_columns<T, LOGK>(A, Y, c1, c2, two);
+  inverse_and_store<T, LOGK>(A, Y, tw, c1, c2, two);
 }
 
 // Forward model, data residual and adjoint of one column pair in one pass
@@ -549,8 +577,7 @@ __global__ void __launch_bounds__(512, 2) k_ax_fused(const __grid_constant__ AxA
   bool warp_tail;
   const int nch = prepare_scatter<T, J>(Y, K, nt, nk, sm, &ch_lo, &ch_hi, &ch_tail, warp_tail);
   scatter_samples<T, J>(A, Y, K, nt, sm, nch, warp_tail);
-  axial_fft_inv<LOGK, T>(Y, K, sc.logK, tw);
-  store_columns<T, LOGK>(A, Y, c1, c2, two);
+  inverse_and_store<T, LOGK>(A, Y, tw, c1, c2, two);
 }
 
 // One thread per (|q| class, k_j): the same evaluation the kernels do on the fly.
