@@ -330,10 +330,7 @@ __device__ __forceinline__ void twiddle_powers(E* a, cplx<T> w1) {
   }
 }
 
-// TRUNC (last pass only, where base = j < NS): output rows in [L/4, 3L/4) are
-// not written (a caller that keeps only the other half of the transform).
-template <int SIGN, int R, int L, int NS, bool HALF_ZERO, int STRIDE, bool TRUNC, typename T,
-          typename E>
+template <int SIGN, int R, int L, int NS, bool HALF_ZERO, int STRIDE, typename T, typename E>
 __device__ __forceinline__ void stockham_pass_ct(E* buf, int col, int b, const cplx<T>* tw) {
   constexpr int NB = 8 / R;          // butterflies per thread
   constexpr int LR = L / R;
@@ -362,30 +359,26 @@ __device__ __forceinline__ void stockham_pass_ct(E* buf, int col, int b, const c
     const int base = (j - k) * R + k;
     const int q0 = prow(base);
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      if (TRUNC && r * NS >= L / 4 && (r + 1) * NS <= 3 * L / 4) continue;
-      buf[prow_at<NS>(base, q0, r) * STRIDE + col] = a[r];
-    }
+    for (int r = 0; r < R; ++r) buf[prow_at<NS>(base, q0, r) * STRIDE + col] = a[r];
   }
   __syncthreads();
 }
 
 // The passes of span NS and up (tw: the segment of span NS).  SKIP_LAST:
 // stop before the last pass (last_pass_regs_ct takes it).
-template <int SIGN, bool HALF_ZERO, bool TRUNC, int L, int NS, int STRIDE, typename T,
-          bool SKIP_LAST = false, typename E>
+template <int SIGN, bool HALF_ZERO, int L, int NS, int STRIDE, typename T, bool SKIP_LAST = false,
+          typename E>
 __device__ __forceinline__ void fft_passes_ct(E* buf, int col, int b, const cplx<T>* tw) {
   if constexpr (NS * 8 <= L) {
     constexpr bool last = NS * 8 == L;
     if constexpr (!(last && SKIP_LAST))
-      stockham_pass_ct<SIGN, 8, L, NS, HALF_ZERO && NS == 1, STRIDE, TRUNC && last, T>(buf, col, b,
-                                                                                       tw);
-    fft_passes_ct<SIGN, HALF_ZERO, TRUNC, L, NS * 8, STRIDE, T, SKIP_LAST>(
-        buf, col, b, tw + (NS > 1 ? NS : 0));
+      stockham_pass_ct<SIGN, 8, L, NS, HALF_ZERO && NS == 1, STRIDE, T>(buf, col, b, tw);
+    fft_passes_ct<SIGN, HALF_ZERO, L, NS * 8, STRIDE, T, SKIP_LAST>(buf, col, b,
+                                                                    tw + (NS > 1 ? NS : 0));
   } else if constexpr (NS * 4 == L && !SKIP_LAST) {
-    stockham_pass_ct<SIGN, 4, L, NS, false, STRIDE, TRUNC, T>(buf, col, b, tw);
+    stockham_pass_ct<SIGN, 4, L, NS, false, STRIDE, T>(buf, col, b, tw);
   } else if constexpr (NS * 2 == L && !SKIP_LAST) {
-    stockham_pass_ct<SIGN, 2, L, NS, false, STRIDE, TRUNC, T>(buf, col, b, tw);
+    stockham_pass_ct<SIGN, 2, L, NS, false, STRIDE, T>(buf, col, b, tw);
   }
 }
 
@@ -433,16 +426,13 @@ __device__ __forceinline__ void last_pass_regs_ct(const E* buf, int col, int b,
 template <int SIGN, bool HALF_ZERO, int LOGL, int STRIDE, typename T, typename E>
 __device__ __forceinline__ void fft_cols_ct(E* buf, int col, int b, const cplx<T>* tw) {
   static_assert(LOGL >= 3, "compile-time transforms start at L = 8");
-  fft_passes_ct<SIGN, HALF_ZERO, false, (1 << LOGL), 1, STRIDE, T>(buf, col, b, tw);
+  fft_passes_ct<SIGN, HALF_ZERO, (1 << LOGL), 1, STRIDE, T>(buf, col, b, tw);
 }
 
-// one column at stride 1 (the axial kernels: every thread of a block of L/8).
-// TRUNC: only output rows [0, L/4) and [3L/4, L) are written (the inverse
-// transform of the adjoint, whose truncation keeps nz = L/2 of them).
-template <int SIGN, bool HALF_ZERO, int LOGL, typename T, bool TRUNC = false, typename E>
+// one column at stride 1 (the axial kernels: every thread of a block of L/8)
+template <int SIGN, bool HALF_ZERO, int LOGL, typename T, typename E>
 __device__ __forceinline__ void fft_smem_ct(E* buf, int b, const cplx<T>* tw) {
-  static_assert(LOGL >= 3, "compile-time transforms start at L = 8");
-  fft_passes_ct<SIGN, HALF_ZERO, TRUNC, (1 << LOGL), 1, 1, T>(buf, 0, b, tw);
+  fft_cols_ct<SIGN, HALF_ZERO, LOGL, 1, T>(buf, 0, b, tw);
 }
 
 }  // namespace isam

@@ -178,19 +178,14 @@ __device__ __forceinline__ cplx<T>* twiddle_table(unsigned char* raw, int K) {
   return reinterpret_cast<cplx<T>*>(raw + size_t(padded_rows(K)) * sizeof(cpair<T>));
 }
 
-// K-point transforms of the block's column pair: the compile-time-length
-// Stockham form when LOGK > 0 (K = 2^LOGK, the sizes the kernels are
-// instantiated for), else the runtime-length one.  The inverse's compile-time
-// form writes only the rows store_columns keeps.  Each ends with a barrier.
+// The forward K-point transform of the block's column pair: the
+// compile-time-length Stockham form when LOGK > 0 (K = 2^LOGK, the sizes the
+// kernels are instantiated for), else the runtime-length one.  Ends with a
+// barrier.  (The inverse is in inverse_and_store.)
 template <int LOGK, typename T>
 __device__ __forceinline__ void axial_fft_fwd(cpair<T>* Y, int K, int logK, const cplx<T>* tw) {
   if constexpr (LOGK > 0) fft_smem_ct<+1, true, LOGK, T>(Y, threadIdx.x, tw);
   else fft_smem<+1, true, T>(Y, 1, 0, threadIdx.x, K, logK, tw, true);
-}
-template <int LOGK, typename T>
-__device__ __forceinline__ void axial_fft_inv(cpair<T>* Y, int K, int logK, const cplx<T>* tw) {
-  if constexpr (LOGK > 0) fft_smem_ct<-1, false, LOGK, T, true>(Y, threadIdx.x, tw);
-  else fft_smem<-1, false, T>(Y, 1, 0, threadIdx.x, K, logK, tw, true);
 }
 
 // K and the block size K/8, as compile-time constants when LOGK > 0
@@ -398,7 +393,7 @@ __device__ __forceinline__ void inverse_and_store(const AxArgs<T>& A, cpair<T>* 
     using C = cplx<T>;
     constexpr int K = 1 << LOGK, nz = K / 2, K8 = K / 8;
     const int b = threadIdx.x;
-    fft_passes_ct<-1, false, false, K, 1, 1, T, true>(Y, 0, b, tw);
+    fft_passes_ct<-1, false, K, 1, 1, T, true>(Y, 0, b, tw);
     C* o1 = A.out + size_t(c1) * nz;
     C* o2 = A.out + size_t(c2) * nz;
     last_pass_regs_ct<-1, LOGK, 1, T>(Y, 0, b, tw, [&](int i, const cpair<T>& y) {
@@ -410,7 +405,7 @@ __device__ __forceinline__ void inverse_and_store(const AxArgs<T>& A, cpair<T>* 
       if (two) o2[n] = cscale(y.b, s);
     });
   } else {
-    axial_fft_inv<LOGK, T>(Y, A.sc.K, A.sc.logK, tw);
+    fft_smem<-1, false, T>(Y, 1, 0, threadIdx.x, A.sc.K, A.sc.logK, tw, true);
     store_columns<T, LOGK>(A, Y, c1, c2, two);
   }
 }

@@ -103,11 +103,6 @@ __global__ void __launch_bounds__(512, 2) k_lat(const __grid_constant__ LatArgs<
   using FWD = std::integral_constant<int, -1>;
   using INV = std::integral_constant<int, +1>;
 
-  // Compile-time LAT_UPDATE: the forward transform's last pass feeds the
-  // stores in registers (the rows a thread stores are that pass's rows).
-  constexpr bool REG_STORE = CT && MODE == LAT_UPDATE;
-  constexpr int CT_L = 1 << LOGL, CT_TP = 1 << LOGTP;
-
   // load the tile: all global loads first, then the shared-memory stores
   {
     V v[8];
@@ -232,20 +227,13 @@ __global__ void __launch_bounds__(512, 2) k_lat(const __grid_constant__ LatArgs<
   }
   if (bad) atomicOr(a.flag, 1);
   __syncthreads();
+  lat_fft(FWD{});
   C* out = static_cast<C*>(a.out);
-  if constexpr (REG_STORE) {
-    fft_passes_ct<-1, false, false, CT_L, 1, CT_TP, T, true>(buf, col, b, tw);
-    last_pass_regs_ct<-1, LOGL, CT_TP, T>(buf, col, b, tw, [&](int i, const V& y) {
-      *reinterpret_cast<V*>(out + gidx(tid + i * nt)) = escale(y, nrm);
-    });
-  } else {
-    lat_fft(FWD{});
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      if (i >= ept) break;
-      const int e = tid + i * nt;
-      *reinterpret_cast<V*>(out + gidx(e)) = escale(buf[sidx(e)], nrm);
-    }
+  for (int i = 0; i < 8; ++i) {
+    if (i >= ept) break;
+    const int e = tid + i * nt;
+    *reinterpret_cast<V*>(out + gidx(e)) = escale(buf[sidx(e)], nrm);
   }
   if (a.partial != nullptr) {
     __shared__ double red[3][32];
