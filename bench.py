@@ -169,8 +169,11 @@ def algorithmic_bytes(cls: str, n_img: int, n_spec: int, real_bytes=4) -> int:
     c = 2 * real_bytes
     return {"ax_fwd": c * (n_img + n_spec),          # read eta_hat, write S
             "ax_adj": c * (n_spec + n_img),          # read R_hat, write G_hat
-            "ax_fused": c * 2 * n_img + c * n_spec // 2,   # eta_hat in, G out, half of F s_d
-            "lat_update": c * n_img * 5}.get(cls)    # G, z1, z2 in; z, eta_hat out
+            "ax_fused": c * 2 * n_img + c * n_spec // 2,   # eta_hat in, u_hat (or G) out,
+                                                            # half of F s_d
+            # u_hat, z^{k-1} in; z^k, eta_hat^{k+1} out (the residual-check
+            # iterations, 1 in 20, also read z^{k-2}: counted as the 4-array pass)
+            "lat_update": c * n_img * 4}.get(cls)
 
 
 # DRAM bytes (read + write) per launch of the current kernels, from the ncu

@@ -65,6 +65,8 @@ enum LatMode : int {
   LAT_UPDATE = 5,    // FISTA step in image space between F^-1 and F
   LAT_GRAD_STEP = 6, // u = eta^k - g/L after F^-1 (no threshold, no F): other priors
   LAT_EXTRAP_FWD = 7,// X = F(z1 + mu (z1 - z2)): the momentum step, then F
+  LAT_UPDATE_U = 8,  // as LAT_UPDATE from u_hat = eta_hat^k - G/L: u = F^-1 u_hat (no z2,
+                     // no norm partials)
 };
 
 template <typename T> struct LatArgs {
@@ -101,6 +103,9 @@ template <typename T> struct AxArgs {
   // first column of each pair is read), and optional per-block ||R||^2
   const cplx<T>* sdh;
   double* partial;
+  // fused kernel: 0 writes G; else writes u_hat = in - u_hat_scale * G (the
+  // lateral spectrum of eta^k - g/L, u_hat_scale = 1/L)
+  T u_hat_scale;
 };
 
 // launchers (return cudaGetLastError())

@@ -281,7 +281,6 @@ template <typename T> isam_status phase_tables(isam_plan* P, Impl<T>& im) {
 template <typename T> isam_status impl_init(isam_plan* P, Impl<T>& im) {
   if (im.ready) return ISAM_OK;
   if (!precision_fits<T>(P)) return ISAM_ERR_UNSUPPORTED;
-  const isam_params& p = P->p;
   // scaling s(n - nz/2) / sqrt(nz)
   {
     std::vector<T> h(P->nz);
@@ -319,7 +318,8 @@ LatArgs<T> lat_args(int B, int L, int M, const void* in, void* out) {
 }
 
 template <typename T> isam_status lat(isam_plan* P, int mode, const LatArgs<T>& a) {
-  const int cls = mode == LAT_UPDATE ? ISAM_KCLASS_LAT_UPDATE : ISAM_KCLASS_LAT_FFT;
+  const int cls = mode == LAT_UPDATE || mode == LAT_UPDATE_U ? ISAM_KCLASS_LAT_UPDATE
+                                                             : ISAM_KCLASS_LAT_FFT;
   return launch(P, cls, [&] { return launch_lat<T>(mode, a, P->stream); });
 }
 
@@ -456,6 +456,12 @@ template <typename T> isam_status fista_iteration(isam_plan* P, Impl<T>& im,
   if (!ehat_out) ehat_out = im.eta_hat;
   AxArgs<T> ax = ax_args<T>(P, im, ehat_in, im.grad);
   ax.sdh = im.sdh;
+  // l1 iterations without the residual check: the fused kernel writes the
+  // lateral spectrum of u = eta^k - g/L (u_hat = eta_hat^k - G/L, linear in
+  // both), so the update needs z^{k-1} only, not z^{k-2} to rebuild eta^k.
+  // The check (Eq. 15) needs g and eta^k apart and takes the G path.
+  const bool from_u = prior == ISAM_PRIOR_L1 && !norms;
+  if (from_u) ax.u_hat_scale = T(1.0 / L);
   ISAM_TRY(launch(P, ISAM_KCLASS_AX_FUSED, [&] { return launch_ax_fused<T>(ax, P->npairs, s); }));
   if (prior == ISAM_PRIOR_HAAR_DEPTH || prior == ISAM_PRIOR_TV) {
     // u^k = eta^k - g/L in image space (in place over G_hat), the Haar prox to
@@ -523,12 +529,12 @@ template <typename T> isam_status fista_iteration(isam_plan* P, Impl<T>& im,
     u.TZ = P->tune_tp;
     u.logTZ = ilog2(P->tune_tp);
   }
-  u.z1 = z1; u.z2 = z2; u.zout = zout; u.w = w; u.nz = P->nz; u.uout = u_out;
+  u.z1 = z1; u.z2 = from_u ? nullptr : z2; u.zout = zout; u.w = w; u.nz = P->nz; u.uout = u_out;
   u.lam_dev = lam_dev; u.lam_scale = lam_scale;
   u.inv_L = T(1.0 / L); u.lam_over_L = T(lam / L); u.mu_prev = T(mu_prev); u.mu = T(mu);
   u.partial = norms ? P->partial : nullptr;
   u.flag = P->flag;
-  ISAM_TRY(lat<T>(P, LAT_UPDATE, u));
+  ISAM_TRY(lat<T>(P, from_u ? LAT_UPDATE_U : LAT_UPDATE, u));
   if (norms) {
     const int nblk = (u.M / (2 * u.TZ)) * u.B;
     ISAM_TRY(launch(P, ISAM_KCLASS_MISC, [&] { return launch_sum3(P->partial, nblk, P->dscal + 1, s); }));
@@ -893,7 +899,6 @@ isam_status isam_plan_create(const isam_params* p, void* stream, isam_plan** out
   isam_status st = ISAM_OK;
   {
     // partial sums: reductions use RED_BLOCKS, the FISTA update one per block
-    const int L = P->ny == 1 ? P->nx : P->ny;
     const int M = P->ny == 1 ? P->nz : P->nx * P->nz;
     const int npairs_max = P->nx * P->ny / 2 + 4;
     P->n_partial = std::max(std::max(RED_BLOCKS, M / 2), npairs_max);   // any update tile

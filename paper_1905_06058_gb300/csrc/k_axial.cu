@@ -363,6 +363,23 @@ __device__ __forceinline__ void scatter_samples(const AxArgs<T>& A, cpair<T>* Y,
   }
 }
 
+// Sample n of both output columns: G = s y, or, when the kernel writes the
+// lateral spectrum of u = eta^k - g/L, u_hat = eta_hat - G/L with eta_hat the
+// kernel's own input (A.in, re-read here: the same samples the block loaded).
+template <typename T>
+__device__ __forceinline__ void put_output(const AxArgs<T>& A, cplx<T>* o1, cplx<T>* o2, int n,
+                                           const cpair<T>& y, T s, int c1, int c2, bool two) {
+  const int nz = A.sc.nz;
+  if (A.u_hat_scale != T(0)) {
+    const T f = s * A.u_hat_scale;
+    o1[n] = csub(A.in[size_t(c1) * nz + n], cscale(y.a, f));
+    if (two) o2[n] = csub(A.in[size_t(c2) * nz + n], cscale(y.b, f));
+  } else {
+    o1[n] = cscale(y.a, s);
+    if (two) o2[n] = cscale(y.b, s);
+  }
+}
+
 // Y (after the e^{-} DFT): truncate to the nz samples, scale, store columns.
 template <typename T, int LOGK>
 __device__ __forceinline__ void store_columns(const AxArgs<T>& A, const cpair<T>* Y, int c1,
@@ -376,8 +393,7 @@ __device__ __forceinline__ void store_columns(const AxArgs<T>& A, const cpair<T>
     if (p < 0) p += K;
     const T s = __ldg(A.tab.scale + n);
     const cpair<T> y = Y[prow(p)];
-    o1[n] = cscale(y.a, s);
-    if (two) o2[n] = cscale(y.b, s);
+    put_output(A, o1, o2, n, y, s, c1, c2, two);
   }
 }
 
@@ -400,9 +416,7 @@ __device__ __forceinline__ void inverse_and_store(const AxArgs<T>& A, cpair<T>* 
       const int p = b + i * K8;
       if (i * K8 >= K / 4 && (i + 1) * K8 <= 3 * K / 4) return;   // rows [K/4, 3K/4)
       const int n = p < K / 4 ? p + nz / 2 : p - (K - nz / 2);
-      const T s = __ldg(A.tab.scale + n);
-      o1[n] = cscale(y.a, s);
-      if (two) o2[n] = cscale(y.b, s);
+      put_output(A, o1, o2, n, y, __ldg(A.tab.scale + n), c1, c2, two);
     });
   } else {
     fft_smem<-1, false, T>(Y, 1, 0, threadIdx.x, A.sc.K, A.sc.logK, tw, true);

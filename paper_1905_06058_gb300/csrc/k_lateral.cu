@@ -10,7 +10,9 @@
 //   eta^k = z^{k-1} + mu_{k-1}(z^{k-1} - z^{k-2}),
 //   z^k = T_{lambda w / L}(eta^k - g/L)                            (Eq. 14),
 //   eta^{k+1} = z^k + mu_k (z^k - z^{k-1}),  eta_hat^{k+1} = F eta^{k+1},
-// with partial norms for the relative residual (Eq. 15).
+// with partial norms for the relative residual (Eq. 15).  LAT_UPDATE_U takes
+// u_hat = eta_hat^k - G/L instead of G (the lateral transform is linear):
+// u = F^{-1} u_hat, and z^{k-2} is not read.
 #include <math.h>
 
 #include <type_traits>
@@ -179,7 +181,10 @@ __global__ void __launch_bounds__(512, 2) k_lat(const __grid_constant__ LatArgs<
     if (bad) atomicOr(a.flag, 1);
     return;
   }
-  // LAT_UPDATE, in two batches of four elements: loads of the iterates first
+  // LAT_UPDATE / LAT_UPDATE_U, in two batches of four elements: loads of the
+  // iterates first.  LAT_UPDATE forms u = eta^k - g/L from the gradient with
+  // eta^k = z1 + mu_prev (z1 - z2); LAT_UPDATE_U transformed u itself.
+  constexpr bool FROM_U = MODE == LAT_UPDATE_U;
   double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
   bool bad = false;
   const T sg = nrm * a.inv_L;
@@ -192,7 +197,7 @@ __global__ void __launch_bounds__(512, 2) k_lat(const __grid_constant__ LatArgs<
       if (h + i >= ept) break;
       const size_t gi = gidx(tid + (h + i) * nt);
       z1v[i] = *reinterpret_cast<const V*>(a.z1 + gi);
-      z2v[i] = *reinterpret_cast<const V*>(a.z2 + gi);
+      if (!FROM_U) z2v[i] = *reinterpret_cast<const V*>(a.z2 + gi);
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -200,19 +205,24 @@ __global__ void __launch_bounds__(512, 2) k_lat(const __grid_constant__ LatArgs<
       const int e = tid + (h + i) * nt;
       const size_t gi = gidx(e);
       const int n0 = int((m_first + 2 * (e & (TP - 1))) & size_t(a.nz - 1));
-      const V g = escale(buf[sidx(e)], sg);                 // g^k = (1/L) A^H(A eta - s)
       const V z1 = z1v[i];
-      const V eta = eadd(z1, escale(esub(z1, z2v[i]), a.mu_prev));
+      V g, eta, u;
+      if (FROM_U) {
+        u = escale(buf[sidx(e)], nrm);
+      } else {
+        g = escale(buf[sidx(e)], sg);                       // g^k = (1/L) A^H(A eta - s)
+        eta = eadd(z1, escale(esub(z1, z2v[i]), a.mu_prev));
+        u = esub(eta, g);
+      }
       const T tau0 = a.w ? lam_over_L * a.w[n0] : lam_over_L;
       const T tau1 = a.w ? lam_over_L * a.w[n0 + 1] : lam_over_L;
-      const V u = esub(eta, g);
       if (a.uout) *reinterpret_cast<V*>(a.uout + gi) = u;
       V z;
       z.a = soft_threshold(u.a, tau0);
       z.b = soft_threshold(u.b, tau1);
       *reinterpret_cast<V*>(a.zout + gi) = z;
       buf[sidx(e)] = eadd(z, escale(esub(z, z1), a.mu));
-      if (a.partial) {
+      if (!FROM_U && a.partial) {
         const V d = esub(z, eta);
         const V dg = eadd(d, g);
         acc0 += double(d.a.x) * d.a.x + double(d.a.y) * d.a.y + double(d.b.x) * d.b.x +
@@ -346,7 +356,8 @@ static cudaError_t launch_lat_tile(const LatArgs<T>& a, cudaStream_t s) {
 template <typename T, int MODE>
 static cudaError_t launch_lat_mode(const LatArgs<T>& a, cudaStream_t s) {
   constexpr bool hot = std::is_same<T, float>::value &&
-                       (MODE == LAT_UPDATE || MODE == LAT_C2C_FWD || MODE == LAT_C2C_INV);
+                       (MODE == LAT_UPDATE || MODE == LAT_UPDATE_U || MODE == LAT_C2C_FWD ||
+                        MODE == LAT_C2C_INV);
   if constexpr (hot) {
     if (!a.r3 && a.L == 1024 && a.TZ == 4) return launch_lat_tile<T, MODE, 10, 2>(a, s);
     if (!a.r3 && a.L == 512 && a.TZ == 8) return launch_lat_tile<T, MODE, 9, 3>(a, s);
@@ -364,6 +375,7 @@ template <typename T> cudaError_t launch_lat(int mode, const LatArgs<T>& a, cuda
     case LAT_UPDATE: return launch_lat_mode<T, LAT_UPDATE>(a, s);
     case LAT_GRAD_STEP: return launch_lat_mode<T, LAT_GRAD_STEP>(a, s);
     case LAT_EXTRAP_FWD: return launch_lat_mode<T, LAT_EXTRAP_FWD>(a, s);
+    case LAT_UPDATE_U: return launch_lat_mode<T, LAT_UPDATE_U>(a, s);
   }
   return cudaErrorInvalidValue;
 }
