@@ -185,7 +185,9 @@ __global__ void __launch_bounds__(512, 2) k_lat(const __grid_constant__ LatArgs<
   // iterates first.  LAT_UPDATE forms u = eta^k - g/L from the gradient with
   // eta^k = z1 + mu_prev (z1 - z2); LAT_UPDATE_U transformed u itself.
   constexpr bool FROM_U = MODE == LAT_UPDATE_U;
-  double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
+  // norm partials: a thread's 8 elements (at most 32 squares per norm) summed
+  // in the plan's precision, the block's threads in double
+  T acc0 = T(0), acc1 = T(0), acc2 = T(0);
   bool bad = false;
   const T sg = nrm * a.inv_L;
   const T lam_over_L = a.lam_dev ? T(a.lam_scale * *a.lam_dev) : a.lam_over_L;
@@ -225,12 +227,9 @@ __global__ void __launch_bounds__(512, 2) k_lat(const __grid_constant__ LatArgs<
       if (!FROM_U && a.partial) {
         const V d = esub(z, eta);
         const V dg = eadd(d, g);
-        acc0 += double(d.a.x) * d.a.x + double(d.a.y) * d.a.y + double(d.b.x) * d.b.x +
-                double(d.b.y) * d.b.y;
-        acc1 += double(g.a.x) * g.a.x + double(g.a.y) * g.a.y + double(g.b.x) * g.b.x +
-                double(g.b.y) * g.b.y;
-        acc2 += double(dg.a.x) * dg.a.x + double(dg.a.y) * dg.a.y + double(dg.b.x) * dg.b.x +
-                double(dg.b.y) * dg.b.y;
+        acc0 += d.a.x * d.a.x + d.a.y * d.a.y + d.b.x * d.b.x + d.b.y * d.b.y;
+        acc1 += g.a.x * g.a.x + g.a.y * g.a.y + g.b.x * g.b.x + g.b.y * g.b.y;
+        acc2 += dg.a.x * dg.a.x + dg.a.y * dg.a.y + dg.b.x * dg.b.x + dg.b.y * dg.b.y;
       }
       bad |= !(isfinite(z.a.x) && isfinite(z.a.y) && isfinite(z.b.x) && isfinite(z.b.y));
     }
@@ -247,9 +246,10 @@ __global__ void __launch_bounds__(512, 2) k_lat(const __grid_constant__ LatArgs<
   }
   if (a.partial != nullptr) {
     __shared__ double red[3][32];
-    acc0 = warp_sum(acc0); acc1 = warp_sum(acc1); acc2 = warp_sum(acc2);
+    const double w0 = warp_sum(double(acc0)), w1 = warp_sum(double(acc1));
+    const double w2 = warp_sum(double(acc2));
     const int wid = tid >> 5, lane = tid & 31;
-    if (lane == 0) { red[0][wid] = acc0; red[1][wid] = acc1; red[2][wid] = acc2; }
+    if (lane == 0) { red[0][wid] = w0; red[1][wid] = w1; red[2][wid] = w2; }
     __syncthreads();
     if (wid == 0) {
       const int nw = (nt + 31) >> 5;

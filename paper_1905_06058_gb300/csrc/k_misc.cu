@@ -97,13 +97,17 @@ cudaError_t minmax_nodes(int nz, int K, int J, const double* f, int n, double* o
 template <typename T, bool MAX>
 __global__ void __launch_bounds__(256) k_reduce1(const cplx<T>* x, size_t n, double* partial) {
   __shared__ double red[8];
+  // |x_i|^2 in the data's precision; the max in it too, sums in double
+  T vm = T(0);
   double v = 0.0;
   for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
        i += size_t(gridDim.x) * blockDim.x) {
     const cplx<T> a = x[i];
-    const double m = double(a.x) * a.x + double(a.y) * a.y;
-    v = MAX ? fmax(v, m) : v + m;
+    const T m = a.x * a.x + a.y * a.y;
+    if (MAX) vm = m > vm ? m : vm;
+    else v += double(m);
   }
+  if (MAX) v = double(vm);
   for (int o = 16; o > 0; o >>= 1) {
     const double t = __shfl_xor_sync(0xffffffffu, v, o);
     v = MAX ? fmax(v, t) : v + t;
