@@ -17,6 +17,8 @@
 // m_z = sum (a / (2 kappa + p)) v (then z0 gradient = dk m_z).
 #include <math.h>
 
+#include <type_traits>
+
 #include "internal.cuh"
 
 namespace isam {
@@ -50,6 +52,7 @@ __global__ void __launch_bounds__(256) k_param_reduce(const __grid_constant__ Pa
   const C* f1 = A.fd ? A.fd + size_t(c1) * nk : nullptr;
   const C* f2 = A.fd ? A.fd + size_t(c2) * nk : nullptr;
   double m[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  float mf[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
   for (int j = threadIdx.x; j < nk; j += blockDim.x) {
     const C S1 = s1[j], S2 = s2[j];
     const C z = mk<T>(0, 0);
@@ -71,17 +74,41 @@ __global__ void __launch_bounds__(256) k_param_reduce(const __grid_constant__ Pa
       s1[j] = Fa1;
       if (two) s2[j] = Fa2;
     }
-    const double dv = double(v);
-    const double t = double(j) - tc;
-    double tp = t;
+    if constexpr (std::is_same<T, float>::value) {
+      // FP32 plans: weights (k_j - k0)^i in float (t = j - (nk-1)/2 is exact)
+      // and the z0 weight a / (2 kappa + sqrt(4 kappa^2 - a)) with only the
+      // cancelling 4 kappa^2 - a in double; a thread's few terms summed in
+      // float (mf), the block's threads in double below
+      const float t = float(j) - float(tc);
+      float tp = t;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      m[i] = fma(tp, dv, m[i]);
-      tp *= t;
+      for (int i = 0; i < 4; ++i) {
+        mf[i] = fmaf(tp, v, mf[i]);
+        tp *= t;
+      }
+      const double kap = A.sc.kap + double(j);
+      const double x = fma(4.0 * kap, kap, -a);
+      if (x > 0.0) {
+        const float d = float(a) / (2.0f * float(kap) + sqrtf(float(x)));
+        mf[4] = fmaf(d, v, mf[4]);
+      }
+    } else {
+      const double dv = double(v);
+      const double t = double(j) - tc;
+      double tp = t;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        m[i] = fma(tp, dv, m[i]);
+        tp *= t;
+      }
+      const double kap = A.sc.kap + double(j);
+      const double x = 4.0 * kap * kap - a;
+      if (x > 0.0) m[4] = fma(a / (2.0 * kap + sqrt(x)), dv, m[4]);
     }
-    const double kap = A.sc.kap + double(j);
-    const double x = 4.0 * kap * kap - a;
-    if (x > 0.0) m[4] = fma(a / (2.0 * kap + sqrt(x)), dv, m[4]);
+  }
+  if constexpr (std::is_same<T, float>::value) {
+#pragma unroll
+    for (int i = 0; i < 5; ++i) m[i] = double(mf[i]);
   }
   __shared__ double red[8][5];
 #pragma unroll
