@@ -505,8 +505,10 @@ __global__ void __launch_bounds__(512, 2) k_ax_adj(const __grid_constant__ AxArg
 // real residual Re(F^{-1} S) - s_d is, column by column,
 //   R(q) = (S(q) + conj(S(-q))) / 2 - F s_d (q),
 // because F(Re v)(q) = (F v(q) + conj(F v(-q))) / 2 and q, -q are the two
-// columns of the pair; then G = N'(conj(phase) R).  F s_d is Hermitian, so
-// only its c1 column is read.  Optionally writes ||R||^2 of the pair.
+// columns of the pair; then G = N'(conj(phase) R), written as is or, when
+// u_hat_scale = 1/L, as u_hat = eta_hat - G/L (put_output).  F s_d is
+// Hermitian, so only its c1 column is read.  Optionally writes ||R||^2 of the
+// pair.
 template <typename T, int J, int LOGK>
 __global__ void __launch_bounds__(512, 2) k_ax_fused(const __grid_constant__ AxArgs<T> A) {
   using C = cplx<T>;
