@@ -100,6 +100,33 @@ def test_weighted_addback_and_lambda_rule(torch):
     plan.close()
 
 
+@pytest.mark.parametrize("prec,tol", [("fp32", 3e-5), ("fp64", 1e-12)])
+def test_u_hat_and_gradient_paths_agree(torch, prec, tol):
+    """Iterations without the residual check take the fused kernel's
+    u_hat = eta_hat - G/L output and the update from it; iterations with the
+    check take G and rebuild eta^k from z^{k-1}, z^{k-2}.  Both compute
+    z^k = T(eta^k - g/L): a solve with the check on every iteration (a tolerance
+    no residual reaches) and one without it agree to rounding, also with
+    weights and on a volume."""
+    from paper_1905_06058_gb300.isam import Plan
+    dt = np.float32 if prec == "fp32" else np.float64
+    for kw, weighted in ((dict(nx=32, nk=64, nz=128), True), (dict(nx=8, ny=8, nk=64, nz=64), False)):
+        wl = I.small_bscan(seed=17, n_points=10, **kw)
+        ref = O.IsamOracle(wl.geom, "nufft")
+        s = I.add_noise(ref.forward(wl.eta), 30.0, np.random.default_rng(17))
+        plan = Plan(wl.geom, precision=prec)
+        w = None
+        if weighted:
+            w = torch.from_numpy(I.depth_weights(wl.geom.nz).astype(dt)).cuda()
+        sd = dev(torch, s, dt)
+        a, ia = plan.solve(sd, lambda_rel=0.02, max_iter=40, L=4.0, w=w)
+        b, ib = plan.solve(sd, lambda_rel=0.02, max_iter=40, L=4.0, w=w, tol=1e-300, check_every=1)
+        plan.close()
+        assert ia["iterations"] == ib["iterations"] == 40
+        r = rel(a.cpu().numpy(), b.cpu().numpy())
+        assert r < tol, r
+
+
 def test_lipschitz_estimate(torch):
     from paper_1905_06058_gb300.isam import Plan
     wl, ref, s, L = problem(seed=13)
