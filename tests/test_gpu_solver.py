@@ -127,6 +127,26 @@ def test_u_hat_and_gradient_paths_agree(torch, prec, tol):
         assert r < tol, r
 
 
+@pytest.mark.parametrize("nx", [256, 512, 1024])
+def test_fista_compile_time_lateral_widths(torch, nx):
+    """Lateral lengths with compile-time update and transform passes
+    (L = 256 and 512 with 8 pair-columns per block, 1024 with 4), against the
+    oracle's FISTA: 20 iterations, FP32, 1e-3."""
+    from paper_1905_06058_gb300.isam import Plan
+    wl = I.small_bscan(nx=nx, nk=64, nz=64, n_points=12, seed=23)
+    ref = O.IsamOracle(wl.geom, "nufft")
+    s = I.add_noise(ref.forward(wl.eta), 30.0, np.random.default_rng(23))
+    # both sides take this L (30 power iterations, 1% margin)
+    L = 1.01 * O.power_iteration(ref.forward, ref.adjoint, I.start_vector(ref.image_shape, 23),
+                                 30, 1e-6)
+    lam = O.lambda_from_data(ref.adjoint, s, 0.02)
+    res = O.fista(ref.forward, ref.adjoint, s, lam, L, max_iter=20, shape=ref.image_shape)
+    plan = Plan(wl.geom, precision="fp32")
+    out, info = plan.solve(dev(torch, s, np.float32), lambda_abs=lam, L=L, max_iter=20)
+    plan.close()
+    assert rel(out.cpu().numpy(), res.eta) < 1e-3
+
+
 def test_lipschitz_estimate(torch):
     from paper_1905_06058_gb300.isam import Plan
     wl, ref, s, L = problem(seed=13)
