@@ -106,6 +106,9 @@ template <typename T> struct AxArgs {
   // fused kernel: 0 writes G; else writes u_hat = in - u_hat_scale * G (the
   // lateral spectrum of eta^k - g/L, u_hat_scale = 1/L)
   T u_hat_scale;
+  // fused kernel, optional: the model spectra S = phase . N(eta_hat)
+  // ([ny][nx][nk], as k_ax_fwd writes them)
+  cplx<T>* s_out;
 };
 
 // launchers (return cudaGetLastError())

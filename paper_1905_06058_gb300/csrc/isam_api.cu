@@ -450,12 +450,14 @@ template <typename T> isam_status fista_iteration(isam_plan* P, Impl<T>& im,
                                                   const double* lam_dev = nullptr,
                                                   double lam_scale = 0.0,
                                                   int prior = ISAM_PRIOR_L1,
-                                                  int prior_iters = 0) {
+                                                  int prior_iters = 0,
+                                                  cplx<T>* s_out = nullptr) {
   cudaStream_t s = P->stream;
   if (!ehat_in) ehat_in = im.eta_hat;
   if (!ehat_out) ehat_out = im.eta_hat;
   AxArgs<T> ax = ax_args<T>(P, im, ehat_in, im.grad);
   ax.sdh = im.sdh;
+  ax.s_out = s_out;
   // l1 iterations without the residual check: the fused kernel writes the
   // lateral spectrum of u = eta^k - g/L (u_hat = eta_hat^k - G/L, linear in
   // both), so the update needs z^{k-1} only, not z^{k-2} to rebuild eta^k.
@@ -1086,7 +1088,8 @@ template <typename T> isam_status calib_buffers(isam_plan* P, Impl<T>& im, int s
     dfree(im.seg);
     im.seg = nullptr;
     im.seg_cap = 0;
-    ISAM_TRY(dalloc(&im.seg, size_t(2 * seg_cap + 1) * P->n_img));
+    // [seg_cap] u^k, [seg_cap + 1] eta_hat^k, [seg_cap] model spectra S^k
+    ISAM_TRY(dalloc(&im.seg, size_t(2 * seg_cap + 1) * P->n_img + size_t(seg_cap) * P->n_spec));
     im.seg_cap = seg_cap;
   }
   if (!im.zA) ISAM_TRY(dalloc(&im.zA, P->n_img));
@@ -1214,6 +1217,8 @@ template <typename T> isam_status unrolled_vjp_impl(isam_plan* P, const T* s_d,
   momentum(K + 1, mu);
   cplx<T>* seg_u = im.seg;              // [C] images u^k
   cplx<T>* seg_eh = im.seg + C * n;     // [C + 1] images eta_hat^k
+  cplx<T>* seg_S = im.seg + size_t(2 * im.seg_cap + 1) * n;   // [C] spectra K eta_hat^k
+  const size_t ns = P->n_spec;
   cplx<T>* zb[3] = {im.cal, im.cal + n, im.cal + 2 * n};
   cplx<T>* ubar = im.cal + 3 * n;
   cplx<T>* bimg = im.cal + 4 * n;
@@ -1240,7 +1245,8 @@ template <typename T> isam_status unrolled_vjp_impl(isam_plan* P, const T* s_d,
     for (int k = k0 + 1; k <= k1; ++k) {
       const int i = k - k0 - 1;
       ISAM_TRY(fista_iteration<T>(P, im, zP, zQ, zQ, w, lam, L, mu[k - 1], mu[k], false,
-                                  seg_eh + i * n, seg_eh + (i + 1) * n, seg_u + i * n));
+                                  seg_eh + i * n, seg_eh + (i + 1) * n, seg_u + i * n, nullptr,
+                                  0.0, ISAM_PRIOR_L1, 0, seg_S + i * ns));
       std::swap(zP, zQ);
     }
     // reverse through the segment
@@ -1257,12 +1263,10 @@ template <typename T> isam_status unrolled_vjp_impl(isam_plan* P, const T* s_d,
       ISAM_TRY(launch(P, ISAM_KCLASS_AX_FWD, [&] {
         return launch_ax_fwd<T>(ax_args<T>(P, im, im.eta_hat, im.spec), P->npairs, s);
       }));
-      ISAM_TRY(launch(P, ISAM_KCLASS_AX_FWD, [&] {
-        return launch_ax_fwd<T>(ax_args<T>(P, im, seg_eh + i * n, im.spec2), P->npairs, s);
-      }));
-      // theta partials; im.spec becomes F(A ubar)
+      // theta partials (S of eta_hat^k: kept by the recompute's fused kernel);
+      // im.spec becomes F(A ubar)
       ISAM_TRY(launch(P, ISAM_KCLASS_MISC, [&] {
-        return launch_param_reduce<T>(param_args<T>(P, im.spec, im.spec2, im.sdh, T(-1), true),
+        return launch_param_reduce<T>(param_args<T>(P, im.spec, seg_S + i * ns, im.sdh, T(-1), true),
                                       P->npairs, s);
       }));
       // b = A^H A ubar
