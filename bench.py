@@ -179,7 +179,7 @@ def algorithmic_bytes(cls: str, n_img: int, n_spec: int, real_bytes=4) -> int:
 # DRAM bytes (read + write) per launch of the current kernels, from the ncu
 # captures summarised in profiles/ (caches flushed before each replayed
 # launch); a kernel without a capture of its current code is left out (None).
-NCU_TRAFFIC = {"ax_fused": 42432256, "lat_update": 34483968}
+NCU_TRAFFIC = {"ax_fused": 42513920, "lat_update": 34335488}
 
 
 def reduce_over_ranks(torch, elapsed, units, world, device):
