@@ -95,7 +95,10 @@ typedef struct {
   double lambda_abs;        /* ... unless lambda_abs > 0, which is used as is     */
   int32_t max_iter;         /* FISTA iterations (>= 1)                            */
   double tol;               /* stop when r_r < tol (Eq. 15); 0 disables the rule  */
-  int32_t check_every;      /* iterations between stop-rule evaluations (>= 1)    */
+  int32_t check_every;      /* iterations between stop-rule evaluations (>= 1);   */
+                            /* an evaluating iteration reads z^{k-2} as well and   */
+                            /* forms the norm partials, the others update from the */
+                            /* lateral spectrum of eta^k - g/L (same iterates)     */
   const void* w_dev;        /* nullable device [nz] weights w (real, plan type)   */
   int32_t residual_addback; /* 1: return z + (1/L) A^H (s_d - A z) (Alg. 1 end)   */
   double L;                 /* step 1/L; 0: power-iteration estimate, cached      */
