@@ -629,7 +629,7 @@ template <typename T> isam_status solve_impl(isam_plan* P, const T* s_d, const i
       CUDA_TRY(cudaMemcpyAsync(P->hscal + 1, P->dscal + 1, 3 * sizeof(double),
                                cudaMemcpyDeviceToHost, s));
       CUDA_TRY(cudaStreamSynchronize(s));
-    harvest_events(P);
+      harvest_events(P);
       const double a = sqrt(P->hscal[1]), g = sqrt(P->hscal[2]), b = sqrt(P->hscal[3]);
       rr = a / (std::max(g, b) + eps);
       if (rr < o->tol) break;
@@ -682,7 +682,7 @@ template <typename T> isam_status solve_impl(isam_plan* P, const T* s_d, const i
   int hflag = 0;
   CUDA_TRY(cudaMemcpyAsync(P->hscal + 4, P->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
-    harvest_events(P);
+  harvest_events(P);
   memcpy(&hflag, P->hscal + 4, sizeof(int));
   isam_status st = hflag ? ISAM_ERR_NONFINITE : ISAM_OK;
   if (info) {
