@@ -3,7 +3,6 @@ only their timings are combined (max of elapsed time, sum of iterations)."""
 import os
 import socket
 
-import pytest
 
 
 def _free_port():

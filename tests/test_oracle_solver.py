@@ -5,7 +5,6 @@ certificate of the weighted-l1 problem, agreement with plain ISTA run to
 convergence, the lambda above which the minimiser is zero, and recovery of
 isolated point scatterers (the paper's sparsity premise).
 """
-import math
 import os
 
 import numpy as np

@@ -7,7 +7,6 @@ dual -1/2||u - tau grad^H p||^2 + 1/2||u||^2 for the feasible p), closes
 with the iteration count; on a tiny real 1-D case the prox matches a brute
 force minimisation of the (exact, nonsmooth) objective."""
 import numpy as np
-import pytest
 
 from oracle import isam_oracle as O
 
