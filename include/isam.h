@@ -188,7 +188,8 @@ isam_status isam_solve_host(isam_plan* plan, const void* s_d_host,
 isam_status isam_lipschitz(isam_plan* plan, int32_t iters, double rtol, const void* v0,
                            double* L_out);
 
-/* max |eta_i| of a device image (used for lambda = c ||A^H s||_inf).  Synchronous. */
+/* max |eta_i| of a device image (used for lambda = c ||A^H s||_inf).  A NaN in
+ * the image makes the result NaN.  Synchronous. */
 isam_status isam_max_abs(isam_plan* plan, const void* eta, double* out);
 
 /* max |x_i| over n complex device elements (FP32: float2, FP64: double2),
@@ -199,10 +200,13 @@ isam_status isam_max_abs(isam_plan* plan, const void* eta, double* out);
  * paper has no counterpart; it is the reduction behind lambda = c ||A^H s||_inf.
  * Scratch is a static device array of ISAM_NOALLOC_MAX_PARTIALS doubles
  * (512 KiB, held by every GPU that loads the library until exit); n above
- * ISAM_NOALLOC_MAX_PARTIALS * 2048 returns ISAM_ERR_UNSUPPORTED.  The first
- * call on a device looks the array's address up (cudaGetSymbolAddress) and
- * must come before any stream capture.  Calls share the array: calls that
- * overlap on the GPU race and must be serialised by the caller. */
+ * ISAM_NOALLOC_MAX_PARTIALS * 2048 returns ISAM_ERR_UNSUPPORTED.  A NaN in x
+ * makes *out NaN.  The first call on a device looks the array's address up
+ * (cudaGetSymbolAddress) and must come before any stream capture; the address
+ * is kept per CUDA context, so after cudaDeviceReset (a new primary context)
+ * the next call looks it up again and must likewise come before any capture.
+ * Calls share the array: calls that overlap on the GPU race and must be
+ * serialised by the caller. */
 #define ISAM_NOALLOC_MAX_PARTIALS 65536
 isam_status isam_max_abs_noalloc(const void* x, int64_t n, int32_t precision, double* out,
                                  void* stream);

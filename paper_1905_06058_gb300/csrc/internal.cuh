@@ -100,9 +100,8 @@ template <typename T> struct AxArgs {
   Poly<T> poly;
   const int2* pairs;
   // fused kernel only: lateral spectrum of the data, F s_d ([ny][nx][nk]; the
-  // first column of each pair is read), and optional per-block ||R||^2
+  // first column of each pair is read)
   const cplx<T>* sdh;
-  double* partial;
   // fused kernel: 0 writes G; else writes u_hat = in - u_hat_scale * G (the
   // lateral spectrum of eta^k - g/L, u_hat_scale = 1/L)
   T u_hat_scale;

@@ -509,8 +509,7 @@ __global__ void __launch_bounds__(512, 2) k_ax_adj(const __grid_constant__ AxArg
 // because F(Re v)(q) = (F v(q) + conj(F v(-q))) / 2 and q, -q are the two
 // columns of the pair; then G = N'(conj(phase) R), written as is or, when
 // u_hat_scale = 1/L, as u_hat = eta_hat - G/L (put_output).  F s_d is
-// Hermitian, so only its c1 column is read.  Optionally writes ||R||^2 of the
-// pair.
+// Hermitian, so only its c1 column is read.
 // WS: also write the model spectra S to A.s_out.
 template <typename T, int J, int LOGK, bool WS>
 __global__ void __launch_bounds__(512, 2) k_ax_fused(const __grid_constant__ AxArgs<T> A) {
@@ -522,7 +521,6 @@ __global__ void __launch_bounds__(512, 2) k_ax_fused(const __grid_constant__ AxA
   V* Y = reinterpret_cast<V*>(smem_raw);
   cplx<T>* tw = twiddle_table<T>(smem_raw, K);
   __shared__ int ch_lo, ch_hi, ch_tail;
-  __shared__ double red[16];
   const int tid = threadIdx.x, nt = axial_threads<LOGK>();
   int c1, c2, mx, my;
   pair_columns(A, c1, c2, mx, my);
@@ -546,7 +544,6 @@ __global__ void __launch_bounds__(512, 2) k_ax_fused(const __grid_constant__ AxA
 
   const Positions<T> pos(A, mx, my);
   Sample<T> sm[NRES];
-  double rr = 0.0;
 #pragma unroll
   for (int rho = 0; rho < NRES; ++rho) {
     const int j = NRES * tid + rho;
@@ -570,10 +567,6 @@ __global__ void __launch_bounds__(512, 2) k_ax_fused(const __grid_constant__ AxA
     }
     const C R1 = csub(cscale(cadd(s1, cconj(s2)), T(0.5)), dq);
     const C R2 = csub(cscale(cadd(s2, cconj(s1)), T(0.5)), cconj(dq));   // F s_d(-q)
-    if (A.partial) {
-      rr += double(R1.x) * R1.x + double(R1.y) * R1.y;
-      if (two) rr += double(R2.x) * R2.x + double(R2.y) * R2.y;
-    }
     if (prop) {
       sm[rho].val.a = cmulc(R1, ph);
       sm[rho].val.b = two ? cmulc(R2, ph) : mk<T>(0, 0);
@@ -582,16 +575,7 @@ __global__ void __launch_bounds__(512, 2) k_ax_fused(const __grid_constant__ AxA
       sm[rho].chunk = 0;
     }
   }
-  if (A.partial) {
-    for (int o = 16; o > 0; o >>= 1) rr += __shfl_xor_sync(0xffffffffu, rr, o);
-    if ((tid & 31) == 0) red[tid >> 5] = rr;
-  }
   __syncthreads();                       // all reads of Y are done
-  if (A.partial && tid == 0) {
-    double t = 0.0;
-    for (int w = 0; w < (nt >> 5); ++w) t += red[w];
-    A.partial[blockIdx.x] = t;
-  }
   bool warp_tail;
   const int nch = prepare_scatter<T, J>(Y, K, nt, nk, sm, &ch_lo, &ch_hi, &ch_tail, warp_tail);
   scatter_samples<T, J>(A, Y, K, nt, sm, nch, warp_tail);

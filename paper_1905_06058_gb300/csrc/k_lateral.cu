@@ -57,9 +57,19 @@ __device__ __forceinline__ double2 soft_threshold(double2 u, double tau) {
   return cscale(u, f);
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
+// Sum of v over the threads of one warp that exist: a block of nt threads
+// (any count, e.g. 8, 24 or 48 for short or 3 * 2^p lateral lengths) has a
+// last warp of n = nt - 32 w lanes, and a shuffle may only name lanes that
+// exist, so the mask holds lanes [0, n) and a lane adds a partner's value only
+// when that partner exists.  The sum lands in lane 0.
+__device__ __forceinline__ double warp_sum_lanes(double v, int n) {
+  const unsigned mask = n >= 32 ? 0xffffffffu : ((1u << n) - 1u);
+  const int lane = threadIdx.x & 31;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int o = 16; o > 0; o >>= 1) {
+    const double t = __shfl_down_sync(mask, v, o);
+    if (lane + o < n) v += t;
+  }
   return v;
 }
 
@@ -246,17 +256,20 @@ __global__ void __launch_bounds__(512, 2) k_lat(const __grid_constant__ LatArgs<
   }
   if (a.partial != nullptr) {
     __shared__ double red[3][32];
-    const double w0 = warp_sum(double(acc0)), w1 = warp_sum(double(acc1));
-    const double w2 = warp_sum(double(acc2));
     const int wid = tid >> 5, lane = tid & 31;
+    const int nw = (nt + 31) >> 5;
+    const int lanes = min(32, nt - 32 * wid);          // lanes of this warp that exist
+    const double w0 = warp_sum_lanes(double(acc0), lanes);
+    const double w1 = warp_sum_lanes(double(acc1), lanes);
+    const double w2 = warp_sum_lanes(double(acc2), lanes);
     if (lane == 0) { red[0][wid] = w0; red[1][wid] = w1; red[2][wid] = w2; }
     __syncthreads();
     if (wid == 0) {
-      const int nw = (nt + 31) >> 5;
       double v0 = lane < nw ? red[0][lane] : 0.0;
       double v1 = lane < nw ? red[1][lane] : 0.0;
       double v2 = lane < nw ? red[2][lane] : 0.0;
-      v0 = warp_sum(v0); v1 = warp_sum(v1); v2 = warp_sum(v2);
+      v0 = warp_sum_lanes(v0, lanes); v1 = warp_sum_lanes(v1, lanes);
+      v2 = warp_sum_lanes(v2, lanes);
       if (lane == 0) {
         const size_t blk = size_t(blockIdx.y) * gridDim.x + blockIdx.x;
         a.partial[3 * blk + 0] = v0;

@@ -92,8 +92,13 @@ cudaError_t minmax_nodes(int nz, int K, int J, const double* f, int n, double* o
 
 // ---------------------------------------------------------------------------
 // Reductions: stage 1 writes one partial per block, stage 2 combines them in a
-// fixed order (deterministic).
+// fixed order (deterministic).  The max lets a NaN through: a NaN anywhere in
+// the input makes the result NaN, so lambda = c ||A^H s||_inf taken from
+// corrupted data is visibly non-finite instead of the max of the rest.
 // ---------------------------------------------------------------------------
+template <typename T> __device__ __forceinline__ T nan_max(T a, T b) {
+  return (b > a || b != b) ? b : a;
+}
 template <typename T, bool MAX>
 __global__ void __launch_bounds__(256) k_reduce1(const cplx<T>* x, size_t n, double* partial) {
   __shared__ double red[8];
@@ -104,19 +109,19 @@ __global__ void __launch_bounds__(256) k_reduce1(const cplx<T>* x, size_t n, dou
        i += size_t(gridDim.x) * blockDim.x) {
     const cplx<T> a = x[i];
     const T m = a.x * a.x + a.y * a.y;
-    if (MAX) vm = m > vm ? m : vm;
+    if (MAX) vm = nan_max(vm, m);
     else v += double(m);
   }
   if (MAX) v = double(vm);
   for (int o = 16; o > 0; o >>= 1) {
     const double t = __shfl_xor_sync(0xffffffffu, v, o);
-    v = MAX ? fmax(v, t) : v + t;
+    v = MAX ? nan_max(v, t) : v + t;
   }
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = red[0];
-    for (int w = 1; w < int(blockDim.x >> 5); ++w) t = MAX ? fmax(t, red[w]) : t + red[w];
+    for (int w = 1; w < int(blockDim.x >> 5); ++w) t = MAX ? nan_max(t, red[w]) : t + red[w];
     partial[blockIdx.x] = t;
   }
 }
@@ -126,12 +131,13 @@ template <bool MAX>
 __global__ void __launch_bounds__(256) k_reduce2(const double* partial, int n, double* out) {
   __shared__ double red[256];
   double v = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) v = MAX ? fmax(v, partial[i]) : v + partial[i];
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    v = MAX ? nan_max(v, partial[i]) : v + partial[i];
   red[threadIdx.x] = v;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
-    for (int i = 0; i < int(blockDim.x); ++i) t = MAX ? fmax(t, red[i]) : t + red[i];
+    for (int i = 0; i < int(blockDim.x); ++i) t = MAX ? nan_max(t, red[i]) : t + red[i];
     *out = sqrt(t);
   }
 }

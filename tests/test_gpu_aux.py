@@ -123,3 +123,23 @@ def test_autotune_cache_file(torch, tmp_path):
             p.close()
     finally:
         del os.environ["ISAM_AUTOTUNE_CACHE"]
+
+
+@pytest.mark.parametrize("prec,cdt", [("fp32", np.complex64), ("fp64", np.complex128)])
+def test_max_abs_propagates_nan(torch, prec, cdt):
+    """lambda = c ||A^H s||_inf must not come silently from corrupted data: a NaN
+    anywhere in the image makes the max NaN; an infinite element gives inf."""
+    from paper_1905_06058_gb300.isam import Plan
+    wl = I.small_bscan(nx=64, nk=256, nz=256, seed=53)
+    plan = Plan(wl.geom, precision=prec)
+    x = I.random_image(plan.image_shape, 53).astype(cdt)
+    ref = float(np.abs(x).max())
+    assert plan.max_abs(torch.from_numpy(x).cuda()) == pytest.approx(ref, rel=1e-6)
+    for pos in ((0, 0, 0), (0, 17, 100), (0, 63, 255)):      # first, inner, last element
+        y = x.copy()
+        y[pos] = complex(np.nan, 0.0)
+        assert np.isnan(plan.max_abs(torch.from_numpy(y).cuda()))
+    y = x.copy()
+    y[0, 5, 7] = complex(0.0, np.inf)
+    assert plan.max_abs(torch.from_numpy(y).cuda()) == np.inf
+    plan.close()

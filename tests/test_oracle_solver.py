@@ -55,6 +55,35 @@ def test_relative_residual_hand_values():
         assert O.relative_residual(z, eta, g, eps=0.0) == pytest.approx(e, rel=1e-15)
 
 
+def test_objective_hand_values():
+    """Eq. 12 on the hand case of tests/golden/objective.txt: a dropped 1/2, a
+    weight applied twice or to the data term, |eta|^2 for |eta| or a sign error
+    in the residual each change every row."""
+    def A(eta):
+        return np.array([eta[0].real + eta[1].real, eta[0].imag, eta[1].real - eta[0].imag])
+
+    eta = np.array([3 + 4j, -1 + 0j])
+    s_d = np.array([1.0, 2.0, -1.0])
+    for lam, w0, w1, e in load("objective.txt"):
+        got = O.objective(A, eta, s_d, lam, np.array([w0, w1]))
+        assert got == pytest.approx(e, rel=1e-15)
+
+
+def test_objective_with_the_isam_operator():
+    """With the real operator: at eta = 0 only 1/2 ||s_d||^2 remains, and with
+    s_d = A eta only the weighted l1 term (to rounding of A eta - s_d)."""
+    wl = I.small_bscan(nx=8, nk=16, nz=16, n_points=4, seed=5)
+    op = O.IsamOracle(wl.geom, "exact")
+    s = op.forward(wl.eta)
+    w = I.depth_weights(op.grid.nz)[None, None, :]
+    zero = np.zeros(op.image_shape, complex)
+    assert O.objective(op.forward, zero, s, 0.3, w) == pytest.approx(0.5 * np.sum(s * s),
+                                                                       rel=1e-14)
+    l1 = float(np.sum(w * np.abs(wl.eta)))
+    assert l1 > 0
+    assert O.objective(op.forward, wl.eta, s, 0.3, w) == pytest.approx(0.3 * l1, rel=1e-12)
+
+
 def tiny_problem(mode="exact", seed=3, nx=4, nk=8, nz=8, n_points=3):
     wl = I.small_bscan(nx=nx, nk=nk, nz=nz, n_points=n_points, seed=seed)
     op = O.IsamOracle(wl.geom, mode)

@@ -40,6 +40,13 @@ def test_noalloc_max_abs_matches_plan_reduction():
             ref = plan.max_abs(x)
             assert got == pytest.approx(ref, rel=1e-12)
             assert got == pytest.approx(float(x.abs().max().cpu()), rel=1e-6)
+        # a NaN in the input reaches the result, and the next call is unaffected
+        y = x.clone()
+        y[0, 40, 3] = complex(float("nan"), 0.0)
+        assert fn(y.data_ptr(), y.numel(), code, out.data_ptr(), stream) == 0
+        assert np.isnan(float(out.cpu()))
+        assert fn(x.data_ptr(), x.numel(), code, out.data_ptr(), stream) == 0
+        assert float(out.cpu()) == pytest.approx(plan.max_abs(x), rel=1e-12)
         # a size whose partials would not fit the static scratch is refused up front
         too_big = 65536 * 2048 + 1
         assert fn(x.data_ptr(), too_big, code, out.data_ptr(), stream) == 6
