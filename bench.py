@@ -40,9 +40,13 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--iters", type=int, default=200)
-    ap.add_argument("--no-extras", action="store_true", help="skip A+A^H, FP64 and volume lines")
-    ap.add_argument("--volume", action="store_true", help="also time the 256^2 x 2048 volume")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the A+A^H, FP64, cuFFT, calibration, batch and volume lines")
+    ap.add_argument("--no-volume", action="store_true", help="skip the 256^2 x 2048 volume line")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="seconds of oracle work per host core in the CPU baseline")
+    ap.add_argument("--cpu-workers", type=int, default=0,
+                    help="host processes for the CPU baseline (0: all cores)")
     ap.add_argument("--no-batch", action="store_true", help="skip the 96-B-scan batch line")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the built-in launch shapes (for runs under a profiler)")
@@ -110,17 +114,23 @@ class Clocks:
 # ----------------------------------------------------------------------------
 # CPU oracle timing (the reported baseline and the reference arm)
 # ----------------------------------------------------------------------------
-def oracle_iteration_rate(seconds: float, nx_slice: int = 64):
-    """FP64 oracle FISTA iterations on a slice of the workload (same band,
-    spectral and depth sampling, dispersion; `nx_slice` of the 1024 A-scans),
-    timed after one warm iteration; the per-iteration time is scaled by
-    1024 / nx_slice (cost is linear in the number of A-scans)."""
+ORACLE_SLICE = 64          # A-scans per oracle process
+
+
+def _oracle_slice_rate(job):
+    """One host process: FP64 oracle FISTA iterations on a 64-A-scan slice of
+    the B-scan workload (same band, spectral and depth sampling, dispersion),
+    timed for `seconds` after one warm iteration.  Returns (iterations,
+    seconds) for that slice."""
+    seconds, index = job
     from oracle import isam_oracle as O
     from paper_1905_06058_gb300 import inputs as I
     wl = I.config2(dtype=np.complex64)
     g = wl.geom
-    g.nx = nx_slice
-    eta = wl.eta[:, :nx_slice].astype(np.complex128)
+    nxs = ORACLE_SLICE
+    lo = (index * nxs) % g.nx
+    g.nx = nxs
+    eta = wl.eta[:, lo:lo + nxs].astype(np.complex128)
     op = O.IsamOracle(g, "nufft")
     s = op.forward(eta)
     lam = 0.01 * np.abs(op.adjoint(s)).max()
@@ -133,8 +143,41 @@ def oracle_iteration_rate(seconds: float, nx_slice: int = 64):
         el = time.perf_counter() - t0
         if el >= seconds and n >= 2:
             break
-    per_iter_full = el / n * (1024 / nx_slice)
-    return 1.0 / per_iter_full, n, el, nx_slice
+    return n, el
+
+
+def oracle_iteration_rate(seconds: float, workers: int = 0):
+    """The FP64 oracle on all host cores: `workers` processes (spawned, one
+    thread each) time FISTA iterations concurrently, each on its own 64-A-scan
+    slice of the 1024 x 2048 B-scan.  The cost of an iteration is linear in the
+    A-scans (per-column NUFFTs; the lateral FFT is a small part), so the
+    full-B-scan rate is the sum of the slices' rates x 64 / 1024."""
+    import multiprocessing as mp
+    workers = workers or os.cpu_count() or 1
+    env = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS",
+                                           "MKL_NUM_THREADS")}
+    for k in env:
+        os.environ[k] = "1"
+    try:
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(workers) as pool:
+            res = pool.map(_oracle_slice_rate, [(seconds, i) for i in range(workers)])
+    finally:
+        for k, v in env.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    slice_rate = sum(n / el for n, el in res)
+    rate = slice_rate * ORACLE_SLICE / 1024
+    n_tot = sum(n for n, _ in res)
+    el_max = max(el for _, el in res)
+    sample = (f"FP64 NumPy oracle (nufft mode, J=6): {workers} host processes, one thread each, "
+              f"each timing FISTA iterations on its own {ORACLE_SLICE}-A-scan slice of the "
+              f"1024x2048 B-scan ({n_tot} slice iterations in {el_max:.1f} s); the summed slice "
+              f"rate scaled by {ORACLE_SLICE}/1024 (extrapolated)")
+    return {"value": rate, "unit": UNIT, "cores": workers, "kind": "oracle", "sample": sample,
+            "extrapolated_from_ascans": ORACLE_SLICE}
 
 
 def run_reference(args):
@@ -143,17 +186,16 @@ def run_reference(args):
         return
     per_step = max(args.cpu_seconds / max(args.steps, 1), 0.5)
     t0 = time.perf_counter()
-    rate, n, el, nxs = oracle_iteration_rate(per_step * args.steps)
-    sample = (f"FP64 NumPy oracle (nufft mode, J=6) FISTA iterations on a {nxs}-A-scan slice of "
-              f"the 1024x2048 B-scan ({n} iterations, {el:.1f} s), scaled x{1024 // nxs}")
+    cpu = oracle_iteration_rate(per_step * args.steps, args.cpu_workers)
+    rate = cpu["value"]
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 / rate * args.iters, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "bscan_1024x2048_fp32", "nx": 1024, "nk": 2048, "nz": 2048,
                        "iters_per_step": args.iters},
-            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": sample},
+            "cpu_baseline": cpu,
+            "extrapolated_from_ascans": ORACLE_SLICE,
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0},
             "wall_s": time.perf_counter() - t0}
@@ -175,10 +217,66 @@ def algorithmic_bytes(cls: str, n_img: int, n_spec: int, real_bytes=4) -> int:
             "lat_update": c * n_img * 4}.get(cls)
 
 
-# DRAM bytes (read + write) per launch of the current kernels, from the ncu
-# captures summarised in profiles/ (caches flushed before each replayed
-# launch); a kernel without a capture of its current code is left out (None).
-NCU_TRAFFIC = {"ax_fused": 42513920, "lat_update": 34335488}
+# Per-launch figures of the dominant kernels from one ncu capture each
+# (profiles/, caches flushed before each replayed launch).  A capture holds
+# for the kernel sources it was taken from: `sha` is the hash of those files
+# (kernel_sources_sha); when the sources have changed since, the figures are
+# reported as null.  dram: dram__bytes_read.sum + dram__bytes_write.sum;
+# table: the part of the reads that is the plan's Stolt table (16 B per
+# (|q| class, k) sample, read once per launch from DRAM when the caches are
+# cold); smem_wavefronts: l1tex__data_pipe_lsu_wavefronts_mem_shared.sum.
+# Volume figures are per launch of the 256 x 256 x 2048 case, scaled from a
+# 128 x 128 x 2048 capture by the column pairs (32,770 / 8,194).
+KERNEL_SOURCES = {
+    "ax_fused": ["k_axial.cuh", "k_axial.cu", "fft_smem.cuh", "internal.cuh", "common.cuh"],
+    "lat_update": ["k_lateral.cu", "fft_smem.cuh", "internal.cuh", "common.cuh"],
+}
+NCU_CAPTURES = {
+    "bscan_1024x2048": {},
+    "volume_256x256x2048": {},
+}
+
+
+def kernel_sources_sha(kind: str) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[kind]:
+        with open(os.path.join(ROOT, "paper_1905_06058_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def capture_of(workload: str, kind: str):
+    c = NCU_CAPTURES.get(workload, {}).get(kind)
+    if c and c["sha"] == kernel_sources_sha(kind):
+        return c
+    return None
+
+
+def roofline_of(kern: dict, kind: str, abytes: int, workload: str, peak: float, peak_src: str,
+                sm_mhz, sms: int, note: str) -> dict:
+    """HBM roofline of one kernel class from the live per-launch CUDA-event
+    average, plus the fraction of the shared-memory pipe (one wavefront per SM
+    per cycle) its captured wavefront count takes at the measured clock."""
+    avg_ms = kern[kind]["ms"] / max(kern[kind]["launches"], 1)
+    achieved = abytes / (avg_ms / 1000.0) / 1e9
+    cap = capture_of(workload, kind)
+    r = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+         "frac": achieved / peak, "traffic": cap["dram"] if cap else None, "kernel": kind,
+         "bytes_per_launch": abytes, "avg_launch_us": avg_ms * 1000.0,
+         "peak_source": peak_src, "note": note}
+    if cap:
+        r["traffic_split"] = {"algorithmic": abytes, "stolt_table": cap.get("table", 0),
+                              "capture_sha": cap["sha"]}
+        if cap.get("smem_wavefronts") and sm_mhz:
+            cyc = sms * sm_mhz * 1e6 * avg_ms / 1000.0
+            r["smem_pipe"] = {"counter": "l1tex__data_pipe_lsu_wavefronts_mem_shared.sum",
+                              "wavefronts_per_launch": cap["smem_wavefronts"],
+                              "sms": sms, "sm_mhz": sm_mhz,
+                              "frac": cap["smem_wavefronts"] / cyc}
+    else:
+        r["traffic_note"] = "no ncu capture of the current kernel sources"
+    return r
 
 
 def reduce_over_ranks(torch, elapsed, units, world, device):
@@ -282,13 +380,13 @@ def run_ours(args):
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     peak = peaks.get("hbm_gbs", 6800.0)
-    avg_ms = kern[dom]["ms"] / max(kern[dom]["launches"], 1)
-    abytes = algorithmic_bytes(dom, n_img, n_spec)
-    achieved = abytes / (avg_ms / 1000.0) / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(dom), "kernel": dom,
-                "bytes_per_launch": abytes, "avg_launch_us": avg_ms * 1000.0,
-                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    roofline = roofline_of(kern, dom, algorithmic_bytes(dom, n_img, n_spec), "bscan_1024x2048",
+                           peak, peak_src, clk.get("sm_mhz"), sms,
+                           "the B-scan's per-iteration working set (~72 MiB) fits the 129 MB "
+                           "L2: L2 is flushed only between 200-iteration steps, so this is "
+                           "algorithmic bytes over time, not DRAM-bound throughput")
     per_iter_bytes = sum(algorithmic_bytes(k, n_img, n_spec) for k in ("ax_fused", "lat_update"))
     iter_gbs = per_iter_bytes * value / max(world, 1) / 1e9
 
@@ -310,18 +408,13 @@ def run_ours(args):
 
     extras = {}
     if not args.no_extras and rank == 0:
-        extras = run_extras(torch, plan, s_d, wl, args, infos[-1]["L"])
+        extras = run_extras(torch, plan, s_d, wl, args, infos[-1]["L"],
+                            dict(peak=peak, peak_src=peak_src, sm_mhz=clk.get("sm_mhz"),
+                                 sms=sms))
 
     if rank == 0:
-        cpu_rate, n, el, nxs = oracle_iteration_rate(args.cpu_seconds) \
-            if world == 1 and not args.no_cpu else (None, 0, 0.0, 64)
-        cpu = None
-        if cpu_rate is not None:
-            cpu = {"value": cpu_rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": f"FP64 NumPy oracle (nufft, J=6): {n} FISTA iterations on a "
-                             f"{nxs}-A-scan slice of this workload in {el:.1f} s, per-iteration "
-                             f"time scaled x{1024 // nxs}; numpy.fft and elementwise work on "
-                             f"one thread"}
+        cpu = oracle_iteration_rate(args.cpu_seconds, args.cpu_workers) \
+            if world == 1 and not args.no_cpu else None
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -343,8 +436,9 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
-def run_extras(torch, plan, s_d, wl, args, L):
-    """A+A^H applications/s, the plain FP64 GPU path and (optionally) the volume."""
+def run_extras(torch, plan, s_d, wl, args, L, roof):
+    """A+A^H applications/s, the plain FP64 GPU path, cuFFT, calibration, the
+    batch and the volume."""
     from paper_1905_06058_gb300 import inputs as I
     from paper_1905_06058_gb300.isam import Plan
     ex = {}
@@ -381,8 +475,8 @@ def run_extras(torch, plan, s_d, wl, args, L):
     ex["calibration"] = run_calibration(torch, args.calib_steps)
     if not args.no_batch:
         ex["batch"] = run_batch(torch, args.batch_iters)
-    if args.volume:
-        ex["volume"] = run_volume(torch)
+    if not args.no_volume:
+        ex["volume"] = run_volume(torch, roof)
     return ex
 
 
@@ -483,6 +577,7 @@ def run_batch(torch, iters: int):
     t0 = time.perf_counter()
     infos = b.run()
     t_graph = time.perf_counter() - t0
+    entry_ms = sorted(b.entry_ms())
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for plan, s, out, kw in ents:
@@ -495,7 +590,12 @@ def run_batch(torch, iters: int):
            "iters_each": iters, "graph_kernels": b.kernel_count(),
            "graph_s": t_graph, "graph_iters_per_s": total / t_graph,
            "sequential_solve_s": t_seq, "sequential_iters_per_s": total / t_seq,
-           "per_solve_latency_s": t_graph,
+           "entry_latency_ms": {"p50": float(np.percentile(entry_ms, 50)),
+                                "p95": float(np.percentile(entry_ms, 95)),
+                                "min": entry_ms[0], "max": entry_ms[-1],
+                                "definition": "device time from the graph's start to the end "
+                                              "of each entry's solve (timing events recorded "
+                                              "in the graph)"},
            "bscan_1024x2048_equivalents": work,
            "statuses_ok": sum(1 for i in infos if i["status"] == 0), "setup_s": setup_s}
     b.close()
@@ -504,7 +604,11 @@ def run_batch(torch, iters: int):
     return res
 
 
-def run_volume(torch):
+def run_volume(torch, roof=None):
+    """The 256 x 256 x 2048 volume (FP32): FISTA iterations/s over a timed
+    40-iteration solve, A + A^H applications/s, and the roofline of its dominant
+    kernel from a second, event-instrumented solve.  Every array is 1 GiB (8x the
+    L2), so the kernels stream from DRAM.  L from 30 power iterations."""
     from paper_1905_06058_gb300 import inputs as I
     from paper_1905_06058_gb300.isam import Plan
     wl = I.config3(dtype=np.complex64)
@@ -516,13 +620,19 @@ def run_volume(torch):
     out = torch.empty(plan.image_shape, dtype=torch.complex64, device="cuda")
     plan.solve(s, out=out, lambda_rel=wl.lambda_rel, max_iter=2, L=L)
     torch.cuda.synchronize()
-    it = 20
+    it = 40
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record()
     plan.solve(s, out=out, lambda_rel=wl.lambda_rel, max_iter=it, L=L)
     b.record()
     torch.cuda.synchronize()
     rate = it / (a.elapsed_time(b) / 1000.0)
+    # per-kernel device time of the same solve, every launch bracketed by events
+    plan.profile(True)
+    plan.solve(s, out=out, lambda_rel=wl.lambda_rel, max_iter=10, L=L)
+    prof = plan.profile_read()
+    plan.profile(False)
+    kern = {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1]}
     # standalone A + A^H applications (C-ABI operators)
     y = torch.empty(plan.spec_shape, dtype=torch.float32, device="cuda")
     plan.forward(out, out=y)
@@ -538,8 +648,14 @@ def run_volume(torch):
     aah = reps / (a.elapsed_time(b) / 1000.0)
     n = wl.geom.nx * wl.geom.ny * wl.geom.nz
     plan.close()
-    return {"workload": wl.name, "iters_per_s": rate, "aah_per_s": aah, "L_estimate_iters": 30,
-            "iteration_gbs_algorithmic": 60 * n * rate / 1e9}
+    res = {"workload": wl.name, "iters_per_s": rate, "aah_per_s": aah, "L_estimate_iters": 30,
+           "timed_iterations": it, "kernels": kern,
+           "iteration_gbs_algorithmic": 60 * n * rate / 1e9}
+    if roof:
+        res["roofline"] = roofline_of(kern, "ax_fused", 20 * n, "volume_256x256x2048",
+                                      roof["peak"], roof["peak_src"], roof["sm_mhz"], roof["sms"],
+                                      "every array is 1 GiB (8x the L2): DRAM-bound inputs")
+    return res
 
 
 def main():

@@ -302,6 +302,11 @@ isam_status isam_batch_create(isam_plan* const* plans, int32_t n, const void* co
 isam_status isam_batch_run(isam_batch* batch, isam_solve_info* info);
 /* Kernel launches recorded in the batch's graph (-1 for NULL). */
 int64_t isam_batch_kernel_count(const isam_batch* batch);
+/* Per-entry latency of the last isam_batch_run: ms[i] = device time from the
+ * start of the graph to the end of entry i's solve (timing events recorded as
+ * nodes of the graph), ms[n].  ISAM_ERR_INVALID before the first run.  The
+ * paper has no counterpart (it solves one B-scan at a time). */
+isam_status isam_batch_entry_ms(const isam_batch* batch, double* ms);
 void isam_batch_destroy(isam_batch* batch);
 
 /* Pick launch shapes by timing the plan's own FISTA iteration (CUDA events on

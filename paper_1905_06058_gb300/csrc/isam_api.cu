@@ -1436,6 +1436,11 @@ struct isam_batch {
   std::vector<double> L;
   std::vector<cudaStream_t> streams;
   std::vector<cudaEvent_t> joins;
+  // timing: recorded as event nodes of the graph, at its start and at the end
+  // of every entry's solve
+  cudaEvent_t t_start = nullptr;
+  std::vector<cudaEvent_t> t_done;
+  bool ran = false;
   cudaEvent_t fork = nullptr;
   cudaStream_t origin = nullptr;
   bool own_origin = false;      // created here (capture cannot use the legacy stream)
@@ -1530,6 +1535,8 @@ void batch_free(isam_batch* B) {
   if (B->graph) cudaGraphDestroy(B->graph);
   for (cudaStream_t st : B->streams) cudaStreamDestroy(st);
   for (cudaEvent_t e : B->joins) cudaEventDestroy(e);
+  for (cudaEvent_t e : B->t_done) cudaEventDestroy(e);
+  if (B->t_start) cudaEventDestroy(B->t_start);
   if (B->fork) cudaEventDestroy(B->fork);
   if (B->own_origin && B->origin) cudaStreamDestroy(B->origin);
   delete B;
@@ -1573,13 +1580,16 @@ isam_status isam_batch_create(isam_plan* const* plans, int32_t n, const void* co
     B->own_origin = st == ISAM_OK;
   }
   if (st == ISAM_OK) st = from_cuda(cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming));
+  if (st == ISAM_OK) st = from_cuda(cudaEventCreate(&B->t_start));
   for (int i = 0; i < n && st == ISAM_OK; ++i) {
     cudaStream_t sx = nullptr;
-    cudaEvent_t ev = nullptr;
+    cudaEvent_t ev = nullptr, td = nullptr;
     st = from_cuda(cudaStreamCreateWithFlags(&sx, cudaStreamNonBlocking));
     if (st == ISAM_OK) B->streams.push_back(sx);
     if (st == ISAM_OK) st = from_cuda(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     if (st == ISAM_OK) B->joins.push_back(ev);
+    if (st == ISAM_OK) st = from_cuda(cudaEventCreate(&td));
+    if (st == ISAM_OK) B->t_done.push_back(td);
   }
   if (st != ISAM_OK) {
     batch_free(B);
@@ -1587,6 +1597,8 @@ isam_status isam_batch_create(isam_plan* const* plans, int32_t n, const void* co
   }
   // record: fork every entry onto its own stream, join them back
   st = from_cuda(cudaStreamBeginCapture(B->origin, cudaStreamCaptureModeRelaxed));
+  if (st == ISAM_OK)
+    st = from_cuda(cudaEventRecordWithFlags(B->t_start, B->origin, cudaEventRecordExternal));
   if (st == ISAM_OK) st = from_cuda(cudaEventRecord(B->fork, B->origin));
   for (int i = 0; i < n && st == ISAM_OK; ++i) {
     isam_plan* P = plans[i];
@@ -1600,6 +1612,8 @@ isam_status isam_batch_create(isam_plan* const* plans, int32_t n, const void* co
                                        static_cast<double2*>(eta_out[i]))
                : batch_enqueue<float>(P, static_cast<const float*>(s_d[i]), &opts[i], B->L[i],
                                       static_cast<float2*>(eta_out[i]));
+    if (st == ISAM_OK)
+      st = from_cuda(cudaEventRecordWithFlags(B->t_done[i], P->stream, cudaEventRecordExternal));
     if (st == ISAM_OK) st = from_cuda(cudaEventRecord(B->joins[i], P->stream));
     if (st == ISAM_OK) st = from_cuda(cudaStreamWaitEvent(B->origin, B->joins[i], 0));
     B->kernels += P->launches - l0;
@@ -1625,6 +1639,7 @@ isam_status isam_batch_run(isam_batch* B, isam_solve_info* info) {
   DeviceGuard g(B->device);
   CUDA_TRY(cudaGraphLaunch(B->exec, B->origin));
   CUDA_TRY(cudaStreamSynchronize(B->origin));
+  B->ran = true;
   isam_status first = ISAM_OK;
   for (int i = 0; i < B->n; ++i) {
     isam_plan* P = B->plans[i];
@@ -1652,6 +1667,18 @@ isam_status isam_batch_run(isam_batch* B, isam_solve_info* info) {
 }
 
 int64_t isam_batch_kernel_count(const isam_batch* B) { return B ? B->kernels : -1; }
+
+isam_status isam_batch_entry_ms(const isam_batch* B, double* ms) {
+  if (!B || !ms) return ISAM_ERR_INVALID;
+  if (!B->ran) return ISAM_ERR_INVALID;
+  DeviceGuard g(B->device);
+  for (int i = 0; i < B->n; ++i) {
+    float t = 0.0f;
+    CUDA_TRY(cudaEventElapsedTime(&t, B->t_start, B->t_done[i]));
+    ms[i] = double(t);
+  }
+  return ISAM_OK;
+}
 
 void isam_batch_destroy(isam_batch* B) {
   if (!B) return;

@@ -92,6 +92,7 @@ _SIGS = {
     "isam_autotune": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32),
                                      ctypes.POINTER(ctypes.c_int32)]),
     "isam_batch_kernel_count": (ctypes.c_int64, [_P]),
+    "isam_batch_entry_ms": (ctypes.c_int, [_P, _P]),
     "isam_batch_destroy": (None, [_P]),
     "isam_set_filter": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
     "isam_set_model": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
@@ -493,6 +494,13 @@ class Batch:
 
     def kernel_count(self) -> int:
         return int(_lib.isam_batch_kernel_count(self._h))
+
+    def entry_ms(self) -> list:
+        """Per-entry latency of the last run: device ms from the graph's start
+        to the end of each entry's solve."""
+        ms = (ctypes.c_double * self.n)()
+        _check(_lib.isam_batch_entry_ms(self._h, ms), "isam_batch_entry_ms")
+        return list(ms)
 
     def close(self):
         if getattr(self, "_h", None):

@@ -152,3 +152,27 @@ def test_batch_mixes_volumes_and_bscans(torch):
     b.close()
     for p, *_ in items:
         p.close()
+
+
+def test_batch_entry_latencies(torch):
+    """isam_batch_entry_ms: per-entry completion times of the last replay, from
+    timing events recorded inside the graph.  Refused before the first run;
+    afterwards every entry's time is positive and no later than the replay's
+    host wall time, and the last entry to finish ends the graph."""
+    import time
+    from paper_1905_06058_gb300.isam import Batch, IsamError
+    ents = entries(torch, seed0=70)
+    b = Batch([(p, sd, res, kw) for p, sd, res, kw, *_ in ents])
+    with pytest.raises(IsamError) as e:
+        b.entry_ms()
+    assert e.value.status == 1
+    b.run()
+    t0 = time.perf_counter()
+    b.run()
+    wall_ms = (time.perf_counter() - t0) * 1e3
+    ms = b.entry_ms()
+    assert len(ms) == len(ents)
+    assert all(0.0 < m <= wall_ms for m in ms), (ms, wall_ms)
+    b.close()
+    for p, *_ in ents:
+        p.close()
