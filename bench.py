@@ -232,8 +232,17 @@ KERNEL_SOURCES = {
     "lat_update": ["k_lateral.cu", "fft_smem.cuh", "internal.cuh", "common.cuh"],
 }
 NCU_CAPTURES = {
-    "bscan_1024x2048": {},
-    "volume_256x256x2048": {},
+    "bscan_1024x2048": {
+        "ax_fused": {"sha": "fdaeb9fbdb9e66e7", "dram": 42398976, "table": 16809984,
+                     "smem_wavefronts": 7944518},
+        "lat_update": {"sha": "a7988f37beab21b4", "dram": 34291200, "table": 0,
+                       "smem_wavefronts": 2904397},
+    },
+    "volume_256x256x2048": {
+        # 128 x 128 x 2048 capture: 636,352,512 B, 137,302,790 wavefronts over 8,194 pairs
+        "ax_fused": {"sha": "fdaeb9fbdb9e66e7", "dram": 2544944083, "table": 0,
+                     "smem_wavefronts": 549110621},
+    },
 }
 
 
