@@ -52,7 +52,8 @@ typedef enum {
   ISAM_ERR_OOM = 2,         /* device allocation failed                     */
   ISAM_ERR_CUDA = 3,        /* a CUDA call or kernel launch failed          */
   ISAM_ERR_NONFINITE = 4,   /* the solve produced a NaN or Inf              */
-  ISAM_ERR_TIMEOUT = 5,     /* a bounded device wait expired                */
+                            /* 5 is not used: no kernel waits on a flag,    */
+                            /* a counter or another kernel                  */
   ISAM_ERR_UNSUPPORTED = 6  /* valid but not implemented (size, J, os)      */
 } isam_status;
 
@@ -187,6 +188,16 @@ isam_status isam_solve_host(isam_plan* plan, const void* s_d_host,
  * Synchronous.  The result is cached in the plan and used by isam_solve. */
 isam_status isam_lipschitz(isam_plan* plan, int32_t iters, double rtol, const void* v0,
                            double* L_out);
+
+/* The data term of the MBIR objective (Eq. 12): *value = 1/2 ||A eta - s_d||^2
+ * (host double, the sum of squares taken in FP64) for a device image eta and
+ * device spectra s_d; when r_out is not NULL the residual spectra A eta - s_d
+ * are written there (device, [ny][nx][nk], the plan's precision; r_out may
+ * alias neither eta nor s_d).  With it a caller differentiates the data
+ * fidelity without leaving the library: d/d eta = A^H r (isam_adjoint),
+ * d/d theta = <dA/dtheta eta, r> (isam_param_grad).  Synchronous. */
+isam_status isam_data_fidelity(isam_plan* plan, const void* eta, const void* s_d, void* r_out,
+                               double* value);
 
 /* max |eta_i| of a device image (used for lambda = c ||A^H s||_inf).  A NaN in
  * the image makes the result NaN.  Synchronous. */

@@ -104,6 +104,40 @@ class UnrolledFista(torch.autograd.Function):
         return s_bar, d_theta, None, None, None, None, None, None
 
 
+class DataFidelity(torch.autograd.Function):
+    """1/2 ||A_theta z - s_d||^2, evaluated by the library (isam_data_fidelity),
+    which also returns the residual r = A_theta z - s_d.  Backward: A^H r for z
+    and <dA/dtheta z, r> for theta, both from the library, times the incoming
+    scalar."""
+
+    @staticmethod
+    def forward(ctx, z, theta, plan: Plan, s_d):
+        _apply_theta(plan, theta)
+        z = z.contiguous()
+        value, r = plan.data_fidelity(z, s_d.contiguous())
+        ctx.plan = plan
+        ctx.save_for_backward(z, theta, r)
+        # a device scalar: autograd then runs this node's backward on the same
+        # device thread as the other nodes of the plan (a plan's calls must not
+        # overlap: they share its workspace)
+        return torch.tensor(value, dtype=torch.float64, device=z.device)
+
+    @staticmethod
+    def backward(ctx, g):
+        z, theta, r = ctx.saved_tensors
+        plan = ctx.plan
+        _apply_theta(plan, theta)
+        gs = float(g)
+        d_z = d_theta = None
+        if ctx.needs_input_grad[0]:
+            d_z = plan.adjoint(r)
+            if gs != 1.0:
+                d_z = d_z * gs
+        if ctx.needs_input_grad[1]:
+            d_theta = torch.from_numpy(plan.param_grad(z, r) * gs)
+        return d_z, d_theta, None, None
+
+
 def model(eta, theta, plan: Plan):
     return IsamA.apply(eta, theta, plan)
 
@@ -118,10 +152,10 @@ def unrolled_fista(s_d, theta, plan: Plan, lam: float, L: float, K: int = 20, ev
 
 
 def data_fidelity(s_d, theta, plan: Plan, lam: float, L: float, K: int, every: int, w=None):
-    """1/2 ||A_theta z^K(theta) - s_d||^2 with z^K the unrolled reconstruction."""
+    """1/2 ||A_theta z^K(theta) - s_d||^2 with z^K the unrolled reconstruction
+    (a float64 device scalar; its value and gradient come from the library)."""
     z = unrolled_fista(s_d, theta, plan, lam, L, K, every, w)
-    r = model(z, theta, plan) - s_d
-    return 0.5 * torch.sum(r.double() * r.double())
+    return DataFidelity.apply(z, theta, plan, s_d)
 
 
 # ----------------------------------------------------------------------------

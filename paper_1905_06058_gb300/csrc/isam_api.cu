@@ -387,6 +387,31 @@ template <typename T> isam_status max_abs_dev(isam_plan* P, const cplx<T>* x, do
   return ISAM_OK;
 }
 
+// 1/2 ||A eta - s_d||^2 (the data term of Eq. 12) and the residual spectra
+// A eta - s_d, in r_out or in the plan's spectra temporary
+template <typename T> isam_status fidelity_impl(isam_plan* P, const void* eta, const T* s_d,
+                                                T* r_out, double* value) {
+  Impl<T>& im = impl_of<T>(P);
+  T* r = r_out;
+  if (!r) {
+    if (!im.s_tmp) ISAM_TRY(dalloc(&im.s_tmp, P->n_spec));
+    r = im.s_tmp;
+  }
+  ISAM_TRY(op_forward<T>(P, eta, r));
+  ISAM_TRY(launch(P, ISAM_KCLASS_MISC, [&] { return launch_rsub<T>(r, s_d, r, P->n_spec, P->stream); }));
+  P->launches += 1;   // two kernels
+  ISAM_TRY(launch(P, ISAM_KCLASS_MISC, [&] {
+    return launch_norm2<T>(reinterpret_cast<const cplx<T>*>(r), P->n_spec / 2, P->partial,
+                           RED_BLOCKS, P->dscal + 5, P->stream);
+  }));
+  CUDA_TRY(cudaMemcpyAsync(P->hscal + 5, P->dscal + 5, sizeof(double), cudaMemcpyDeviceToHost,
+                           P->stream));
+  CUDA_TRY(cudaStreamSynchronize(P->stream));
+  harvest_events(P);
+  *value = 0.5 * P->hscal[5] * P->hscal[5];
+  return ISAM_OK;
+}
+
 // power iteration for ||A^H A|| in precision T
 template <typename T> isam_status power_iteration(isam_plan* P, int iters, double rtol,
                                                   const void* v0, int v0_double, double* L_out) {
@@ -876,7 +901,6 @@ const char* isam_status_string(isam_status s) {
     case ISAM_ERR_OOM: return "out of device memory";
     case ISAM_ERR_CUDA: return "CUDA error";
     case ISAM_ERR_NONFINITE: return "non-finite value in the solve";
-    case ISAM_ERR_TIMEOUT: return "device wait timed out";
     case ISAM_ERR_UNSUPPORTED: return "unsupported size or option";
   }
   return "unknown status";
@@ -1039,6 +1063,18 @@ isam_status isam_lipschitz(isam_plan* P, int32_t iters, double rtol, const void*
   P->L_cache = L;
   *L_out = L;
   return ISAM_OK;
+}
+
+isam_status isam_data_fidelity(isam_plan* P, const void* eta, const void* s_d, void* r_out,
+                               double* value) {
+  if (!P || !eta || !s_d || !value) return ISAM_ERR_INVALID;
+  DeviceGuard g(P->device);
+  P->launches = 0;
+  if (P->p.precision == ISAM_FP64)
+    return fidelity_impl<double>(P, eta, static_cast<const double*>(s_d),
+                                 static_cast<double*>(r_out), value);
+  return fidelity_impl<float>(P, eta, static_cast<const float*>(s_d), static_cast<float*>(r_out),
+                              value);
 }
 
 isam_status isam_max_abs(isam_plan* P, const void* eta, double* out) {

@@ -25,8 +25,7 @@ ISAM_FP32, ISAM_FP64 = 0, 1
 ISAM_FLAG_NO_STOLT_TABLE = 1
 ISAM_FLAG_AXIAL_MODEL = 4
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "CUDA error",
-          4: "non-finite value in the solve", 5: "device wait timed out",
-          6: "unsupported size or option"}
+          4: "non-finite value in the solve", 6: "unsupported size or option"}
 
 
 class IsamParams(ctypes.Structure):
@@ -92,6 +91,7 @@ _SIGS = {
     "isam_autotune": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32),
                                      ctypes.POINTER(ctypes.c_int32)]),
     "isam_batch_kernel_count": (ctypes.c_int64, [_P]),
+    "isam_data_fidelity": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
     "isam_batch_entry_ms": (ctypes.c_int, [_P, _P]),
     "isam_batch_destroy": (None, [_P]),
     "isam_set_filter": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
@@ -252,6 +252,20 @@ class Plan:
                                  self._dev(out, self.real_dtype, self.spec_shape, "out")),
                "isam_forward")
         return out
+
+    def data_fidelity(self, eta, s_d, r_out=None):
+        """isam_data_fidelity: (1/2 ||A eta - s_d||^2, residual spectra A eta - s_d)."""
+        import torch
+        self._sync_stream()
+        if r_out is None:
+            r_out = torch.empty(self.spec_shape, dtype=self.real_dtype, device=eta.device)
+        v = ctypes.c_double()
+        _check(_lib.isam_data_fidelity(
+            self._h, self._dev(eta, self.cplx_dtype, self.image_shape, "eta"),
+            self._dev(s_d, self.real_dtype, self.spec_shape, "s_d"),
+            self._dev(r_out, self.real_dtype, self.spec_shape, "r_out"), ctypes.byref(v)),
+            "isam_data_fidelity")
+        return v.value, r_out
 
     def adjoint(self, s, out=None):
         """eta = A^H s."""

@@ -129,6 +129,7 @@ def test_null_arguments(isam):
     assert lib.isam_set_allocator(None, None, None) == 0
     assert lib.isam_batch_create(None, 0, None, None, None, None, None) == 1
     assert lib.isam_batch_entry_ms(None, None) == 1
+    assert lib.isam_data_fidelity(None, None, None, None, None) == 1
     assert lib.isam_set_filter(None, None) == 1
     assert lib.isam_unrolled_checkpoint_images(20, 5) == 8
     assert lib.isam_unrolled_checkpoint_images(0, 5) == -1

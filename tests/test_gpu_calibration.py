@@ -235,3 +235,32 @@ def test_calibration_recovers_hidden_theta(torch):
     # the annealed step settles: the last loss is within 5 % of the best seen
     assert res.losses[-1] <= 1.05 * res.best_loss, (res.losses[-1], res.best_loss)
     assert np.all(err1 < 0.2 * err0), (err0, err1)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("fp64", 1e-6)])
+def test_data_fidelity_matches_oracle(torch, prec, tol):
+    """isam_data_fidelity: 1/2 ||A eta - s||^2 and the residual A eta - s against
+    the oracle (Eq. 12 data term, per-application bars), and the autograd
+    Function built on it returns exactly A^H r and <dA/dtheta z, r>."""
+    from paper_1905_06058_gb300 import calib
+    from paper_1905_06058_gb300.isam import Plan
+    wl = I.small_bscan(nx=32, nk=128, nz=128, seed=61, n_points=10)
+    op = O.IsamOracle(wl.geom, "nufft")
+    s = I.add_noise(op.forward(wl.eta), 20.0, np.random.default_rng(61))
+    eta = wl.eta + 0.3 * I.random_image(op.image_shape, 62)
+    r_ref = op.forward(eta) - s
+    ct, rt = types(prec)
+    plan = Plan(wl.geom, precision=prec)
+    ed, sd = dev(torch, eta, ct), dev(torch, s, rt)
+    value, r = plan.data_fidelity(ed, sd)
+    assert np.linalg.norm(r.cpu().numpy() - r_ref) <= tol * np.linalg.norm(r_ref)
+    assert value == pytest.approx(0.5 * np.sum(r_ref * r_ref), rel=2 * tol)
+    z = ed.clone().requires_grad_(True)
+    th = torch.tensor(list(wl.geom.disp) + [wl.geom.z0], dtype=torch.float64,
+                      requires_grad=True)
+    loss = calib.DataFidelity.apply(z, th, plan, sd)
+    assert float(loss) == value
+    loss.backward()
+    assert torch.equal(z.grad, plan.adjoint(r))
+    assert np.array_equal(th.grad.numpy(), plan.param_grad(ed, r))
+    plan.close()
