@@ -92,8 +92,10 @@ struct isam_plan {
 namespace {
 
 constexpr int RED_BLOCKS = 1024;
-// Stolt position/phase tables are kept when at most this large (B-scans);
-// larger geometries (volumes) evaluate positions in the kernels.
+// Stolt position/phase tables are kept when at most this large or at most
+// one image array of the plan (16 B per (|q| class, k) sample against 8 or 16
+// B per image sample: every B-scan and the 256^2 x 2048 volume); larger
+// geometries evaluate positions in the kernels.
 constexpr size_t kStoltTableMaxBytes = size_t(64) << 20;
 // power iteration used when the caller gives no L: the top eigenvalues of
 // A^H A lie close together, so convergence takes hundreds of steps
@@ -267,7 +269,8 @@ template <typename T> isam_status phase_tables(isam_plan* P, Impl<T>& im) {
   }
   {
     const size_t bytes = rows * P->nk * sizeof(StoltEntry<T>);
-    if (bytes <= kStoltTableMaxBytes && !(p.flags & ISAM_FLAG_NO_STOLT_TABLE)) {
+    const size_t cap = std::max(kStoltTableMaxBytes, P->n_img * sizeof(cplx<T>));
+    if (bytes <= cap && !(p.flags & ISAM_FLAG_NO_STOLT_TABLE)) {
       if (!im.tab.stab) ISAM_TRY(dalloc(&im.tab.stab, rows * P->nk));
       AxArgs<T> a{};
       a.sc = P->sc;
