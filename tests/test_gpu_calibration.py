@@ -259,7 +259,7 @@ def test_data_fidelity_matches_oracle(torch, prec, tol):
     th = torch.tensor(list(wl.geom.disp) + [wl.geom.z0], dtype=torch.float64,
                       requires_grad=True)
     loss = calib.DataFidelity.apply(z, th, plan, sd)
-    assert float(loss) == value
+    assert float(loss.detach()) == value
     loss.backward()
     assert torch.equal(z.grad, plan.adjoint(r))
     assert np.array_equal(th.grad.numpy(), plan.param_grad(ed, r))
