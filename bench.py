@@ -228,7 +228,8 @@ def algorithmic_bytes(cls: str, n_img: int, n_spec: int, real_bytes=4) -> int:
 # Volume figures are per launch of the 256 x 256 x 2048 case, scaled from a
 # 128 x 128 x 2048 capture by the column pairs (32,770 / 8,194).
 KERNEL_SOURCES = {
-    "ax_fused": ["k_axial.cuh", "k_axial.cu", "fft_smem.cuh", "internal.cuh", "common.cuh"],
+    "ax_fused": ["k_axial.cuh", "k_axial.cu", "fft_smem.cuh", "fft_col16.cuh", "internal.cuh",
+                 "common.cuh"],
     "lat_update": ["k_lateral.cu", "fft_smem.cuh", "internal.cuh", "common.cuh"],
 }
 NCU_CAPTURES = {

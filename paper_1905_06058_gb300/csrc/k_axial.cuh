@@ -24,6 +24,7 @@
 
 #include <limits.h>
 
+#include "fft_col16.cuh"
 #include "fft_smem.cuh"
 #include "internal.cuh"
 
@@ -382,6 +383,17 @@ __device__ __forceinline__ void put_output(const AxArgs<T>& A, cplx<T>* o1, cplx
   }
 }
 
+// Sample n of one output column (column index col of the plan's layout): the
+// single-column form of put_output.
+template <typename T>
+__device__ __forceinline__ void put_output1(const AxArgs<T>& A, cplx<T>* o, int col, int n,
+                                            const cplx<T>& y, T s) {
+  if (A.u_hat_scale != T(0))
+    o[n] = csub(A.in[size_t(col) * A.sc.nz + n], cscale(y, s * A.u_hat_scale));
+  else
+    o[n] = cscale(y, s);
+}
+
 // Y (after the e^{-} DFT): truncate to the nz samples, scale, store columns.
 template <typename T, int LOGK>
 __device__ __forceinline__ void store_columns(const AxArgs<T>& A, const cpair<T>* Y, int c1,
@@ -526,21 +538,42 @@ __global__ void __launch_bounds__(512, 2) k_ax_fused(const __grid_constant__ AxA
   pair_columns(A, c1, c2, mx, my);
   const bool two = c2 != c1;
   if (tid == 0) { ch_lo = INT_MAX; ch_hi = INT_MIN; }
+  // FP32 at K = 2048, 4096: column-split radix-16 transforms (fft_col16.cuh)
+  constexpr bool COL16 = std::is_same<T, float>::value && LOGK >= 11;
   // Programmatic dependent launch: the next kernel in the stream may start its
   // own prologue on SMs this grid leaves idle; this grid builds its twiddles,
   // then waits for the previous kernel before touching global data.
   cudaTriggerProgrammaticLaunchCompletion();
-  build_twiddles<T>(tw, K, sc.logK);
+  if constexpr (COL16) c16::build_twiddles<(LOGK >= 11 ? LOGK : 11)>(reinterpret_cast<float4*>(tw));
+  else build_twiddles<T>(tw, K, sc.logK);
   cudaGridDependencySynchronize();
-  // F s_d at this pair's samples, fetched before the transforms need them
+  // F s_d at this pair's samples, fetched before the transforms need them (the
+  // column-split transforms take them after the forward transform: their
+  // registers are needed there)
   const C* d1 = A.sdh + size_t(c1) * nk;
   C dqv[NRES];
+  if constexpr (!COL16) {
 #pragma unroll
-  for (int rho = 0; rho < NRES; ++rho) {
-    const int j = NRES * tid + rho;
-    dqv[rho] = j < nk ? d1[j] : mk<T>(0, 0);
+    for (int rho = 0; rho < NRES; ++rho) {
+      const int j = NRES * tid + rho;
+      dqv[rho] = j < nk ? d1[j] : mk<T>(0, 0);
+    }
   }
-  load_and_fft<T, LOGK>(A, Y, tw, c1, c2, two);
+  if constexpr (COL16) {
+    const int c = tid & 1;
+    const C* x = c == 0 ? A.in + size_t(c1) * (K / 2) : (two ? A.in + size_t(c2) * (K / 2) : nullptr);
+    c16::forward<(LOGK >= 11 ? LOGK : 11)>(reinterpret_cast<float2*>(Y),
+                                           reinterpret_cast<const float2*>(x),
+                                           reinterpret_cast<const float*>(A.tab.scale),
+                                           reinterpret_cast<const float4*>(tw));
+#pragma unroll
+    for (int rho = 0; rho < NRES; ++rho) {
+      const int j = NRES * tid + rho;
+      dqv[rho] = j < nk ? d1[j] : mk<T>(0, 0);
+    }
+  } else {
+    load_and_fft<T, LOGK>(A, Y, tw, c1, c2, two);
+  }
 
   const Positions<T> pos(A, mx, my);
   Sample<T> sm[NRES];
@@ -579,7 +612,24 @@ __global__ void __launch_bounds__(512, 2) k_ax_fused(const __grid_constant__ AxA
   bool warp_tail;
   const int nch = prepare_scatter<T, J>(Y, K, nt, nk, sm, &ch_lo, &ch_hi, &ch_tail, warp_tail);
   scatter_samples<T, J>(A, Y, K, nt, sm, nch, warp_tail);
-  inverse_and_store<T, LOGK>(A, Y, tw, c1, c2, two);
+  if constexpr (COL16) {
+    // rows j + i K/16 of this thread's column; rows [K/4, 3K/4) are dropped
+    constexpr int KK = 1 << (LOGK >= 11 ? LOGK : 11), nz = KK / 2, K16 = KK / 16;
+    const int c = tid & 1, jb = tid >> 1;
+    const int col = c ? c2 : c1;
+    C* o = A.out + size_t(col) * nz;
+    const bool keep = c == 0 || two;
+    c16::inverse<(LOGK >= 11 ? LOGK : 11)>(
+        reinterpret_cast<float2*>(Y), reinterpret_cast<const float4*>(tw),
+        [&](int i, const float2& y) {
+          if (!keep || (i >= 4 && i < 12)) return;
+          const int p = jb + i * K16;
+          const int n = i < 4 ? p + nz / 2 : p - (KK - nz / 2);
+          put_output1(A, o, col, n, reinterpret_cast<const C&>(y), __ldg(A.tab.scale + n));
+        });
+  } else {
+    inverse_and_store<T, LOGK>(A, Y, tw, c1, c2, two);
+  }
 }
 
 // One thread per (|q| class, k_j): the same evaluation the kernels do on the fly.
