@@ -25,9 +25,10 @@ namespace c16 {
 
 enum { P8 = 8, P16 = 16 };
 
-// float2 index of (row, column c) in layout PAD
-template <int PAD> __device__ __forceinline__ int el(int row, int c) {
-  return 2 * (PAD == P8 ? row + (row >> 3) : row + (row >> 4)) + c;
+// float2 index of (row, column c) in layout PAD, W float2 columns per row
+// (2 for the axial column pair, 2 TP for a lateral tile of TP column pairs)
+template <int PAD, int W = 2> __device__ __forceinline__ int el(int row, int c) {
+  return W * (PAD == P8 ? row + (row >> 3) : row + (row >> 4)) + c;
 }
 
 // multiply by W16^1 = e^{SIGN 2 pi i / 16} and W16^3
@@ -84,7 +85,9 @@ __device__ __forceinline__ void dft16(float2* a) {
 
 template <int SIGN, int R> __device__ __forceinline__ void dft_r(float2* a) {
   if constexpr (R == 16) dft16<SIGN, false>(a);
-  else dft8<SIGN>(a);
+  else if constexpr (R == 8) dft8<SIGN>(a);
+  else if constexpr (R == 4) dft4<SIGN>(a[0], a[1], a[2], a[3]);
+  else dft2<SIGN>(a[0], a[1]);
 }
 
 // Twiddle table: per pass with span NS > 1 (radix R), entry k < NS holds
@@ -110,14 +113,17 @@ template <int LOGK> __device__ __forceinline__ void build_twiddles(float4* tw) {
   __syncthreads();
 }
 
-// a[r] *= w^r, r = 1 .. R-1 (R = 8 or 16), from (w, w^4) (conjugated for SIGN > 0)
+// a[r] *= w^r, r = 1 .. R-1 (R = 2, 4, 8 or 16), from (w, w^4) (conjugated
+// for SIGN > 0)
 template <int SIGN, int R> __device__ __forceinline__ void twiddle(float2* a, float4 t) {
   float2 w1 = make_float2(t.x, t.y), w4 = make_float2(t.z, t.w);
   if (SIGN > 0) { w1.y = -w1.y; w4.y = -w4.y; }
-  const float2 w2 = cmul(w1, w1), w3 = cmul(w2, w1);
   a[1] = cmul(a[1], w1);
+  if constexpr (R == 2) return;
+  const float2 w2 = cmul(w1, w1), w3 = cmul(w2, w1);
   a[2] = cmul(a[2], w2);
   a[3] = cmul(a[3], w3);
+  if constexpr (R == 4) return;
   a[4] = cmul(a[4], w4);
   a[5] = cmul(a[5], cmul(w4, w1));
   a[6] = cmul(a[6], cmul(w4, w2));
@@ -136,10 +142,10 @@ template <int SIGN, int R> __device__ __forceinline__ void twiddle(float2* a, fl
 }
 
 // One Stockham pass of radix R and span NS over the column c of a length-L
-// pair buffer: this thread's 16 / R butterflies j = b + u L/16 read rows
-// j + r L/R (layout IN), barrier, write rows (j - k) R + k + r NS (layout
+// buffer of W columns: this thread's 16 / R butterflies j = b + u L/16 read
+// rows j + r L/R (layout IN), barrier, write rows (j - k) R + k + r NS (layout
 // OUT), barrier.  tw: this pass's segment (unused for NS = 1).
-template <int SIGN, int R, int L, int NS, int IN, int OUT>
+template <int SIGN, int R, int L, int NS, int IN, int OUT, int W = 2>
 __device__ __forceinline__ void pass(float2* Y, int b, int c, const float4* tw) {
   constexpr int NB = 16 / R, LR = L / R, L16 = L / 16;
   float2 v[16];
@@ -147,7 +153,7 @@ __device__ __forceinline__ void pass(float2* Y, int b, int c, const float4* tw) 
   for (int u = 0; u < NB; ++u) {
     const int j = b + u * L16;
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[u * R + r] = Y[el<IN>(j + r * LR, c)];
+    for (int r = 0; r < R; ++r) v[u * R + r] = Y[el<IN, W>(j + r * LR, c)];
   }
   __syncthreads();
 #pragma unroll
@@ -159,7 +165,7 @@ __device__ __forceinline__ void pass(float2* Y, int b, int c, const float4* tw) 
     dft_r<SIGN, R>(a);
     const int base = (j - k) * R + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) Y[el<OUT>(base + r * NS, c)] = a[r];
+    for (int r = 0; r < R; ++r) Y[el<OUT, W>(base + r * NS, c)] = a[r];
   }
   __syncthreads();
 }
@@ -208,6 +214,54 @@ __device__ __forceinline__ void inverse(float2* Y, const float4* tw, Emit emit) 
     dft_r<-1, R>(a);
 #pragma unroll
     for (int r = 0; r < R; ++r) emit(u + r * NB, a[r]);   // row jj + 256 r = j + (u + r NB) K/16
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Lateral transforms of a tile of W = 2 TP columns (k_lat's compile-time
+// instances), L = 1024 = 16 * 4 * 16 or 256 = 16 * 16: thread t owns column
+// c = t mod W of butterfly j = t / W, the tile's rows in layout P8 before and
+// after the transform, P16 between its passes.
+// ---------------------------------------------------------------------------
+// (span, radix) of the passes and the twiddle segments (span > 1, in pass
+// order): L = 1024: (1, 16) (16, 4) (64, 16), segments of 16 and 64 entries;
+// the radix-4 pass sits at span 16, where a thread's four butterflies
+// j = b + 64 u share k = j mod 16 and so one twiddle entry.  L = 256: (1, 16)
+// (16, 16), one segment of 16.
+template <int LOGL> struct LatPasses;
+template <> struct LatPasses<10> {
+  static constexpr int entries = 16 + 64;
+};
+template <> struct LatPasses<8> {
+  static constexpr int entries = 16;
+};
+
+template <int LOGL> __device__ __forceinline__ void build_lat_twiddles(float4* tw) {
+  for (int e = threadIdx.x; e < LatPasses<LOGL>::entries; e += blockDim.x) {
+    const int ns = e < 16 ? 16 : 64, k = e < 16 ? e : e - 16;
+    const int R = e < 16 ? (LOGL == 10 ? 4 : 16) : 16;
+    float s1, c1, s4, c4;
+    sincospif(float(2 * k) / float(ns * R), &s1, &c1);
+    sincospif(float(8 * k) / float(ns * R), &s4, &c4);
+    tw[e] = make_float4(c1, -s1, c4, -s4);
+  }
+  __syncthreads();
+}
+
+// In-place unnormalised transform (SIGN -1: e^{-}) of the tile's W columns,
+// rows in layout P8 before and after.  Every thread of the block calls it;
+// it ends with a barrier.
+template <int SIGN, int LOGL, int W>
+__device__ __forceinline__ void lat_transform(float2* Y, const float4* tw) {
+  constexpr int L = 1 << LOGL;
+  const int c = threadIdx.x & (W - 1), j = threadIdx.x / W;
+  if constexpr (LOGL == 10) {
+    pass<SIGN, 16, L, 1, P8, P16, W>(Y, j, c, tw);
+    pass<SIGN, 4, L, 16, P16, P16, W>(Y, j, c, tw);
+    pass<SIGN, 16, L, 64, P16, P8, W>(Y, j, c, tw + 16);
+  } else {
+    pass<SIGN, 16, L, 1, P8, P16, W>(Y, j, c, tw);
+    pass<SIGN, 16, L, 16, P16, P8, W>(Y, j, c, tw);
   }
 }
 

@@ -17,6 +17,7 @@
 
 #include <type_traits>
 
+#include "fft_col16.cuh"
 #include "fft_smem.cuh"
 #include "internal.cuh"
 
@@ -91,10 +92,13 @@ __global__ void __launch_bounds__(512, 2) k_lat(const __grid_constant__ LatArgs<
   constexpr bool CT = LOGL > 0;
   const int TP = a.TZ, L = CT ? (1 << LOGL) : a.L, logTP = a.logTZ;
   cplx<T>* tw = reinterpret_cast<cplx<T>*>(buf + size_t(padded_rows(L)) * TP);
+  // FP32 at L = 1024 and 256: column-split radix-16 transforms (fft_col16.cuh)
+  constexpr bool COL16 = CT && std::is_same<T, float>::value && (LOGL == 10 || LOGL == 8);
   // programmatic dependent launch: let the next kernel start its prologue,
   // build the twiddles, then wait for the previous kernel's results
   cudaTriggerProgrammaticLaunchCompletion();
-  build_twiddles<T>(tw, L, CT ? LOGL : a.logL, CT ? 0 : a.r3);
+  if constexpr (COL16) c16::build_lat_twiddles<LOGL>(reinterpret_cast<float4*>(tw));
+  else build_twiddles<T>(tw, L, CT ? LOGL : a.logL, CT ? 0 : a.r3);
   cudaGridDependencySynchronize();
   const int col = tid & (TP - 1), b = tid >> logTP;
   const size_t M = size_t(a.M);
@@ -109,7 +113,10 @@ __global__ void __launch_bounds__(512, 2) k_lat(const __grid_constant__ LatArgs<
   auto sidx = [&](int e) { return prow(e >> logTP) * TP + (e & (TP - 1)); };
   auto lat_fft = [&](auto sign) {
     constexpr int SIGN = decltype(sign)::value;
-    if constexpr (CT) fft_cols_ct<SIGN, false, LOGL, (1 << LOGTP), T>(buf, col, b, tw);
+    if constexpr (COL16)
+      c16::lat_transform<SIGN, LOGL, 2 * (1 << LOGTP)>(reinterpret_cast<float2*>(buf),
+                                                        reinterpret_cast<const float4*>(tw));
+    else if constexpr (CT) fft_cols_ct<SIGN, false, LOGL, (1 << LOGTP), T>(buf, col, b, tw);
     else fft_smem<SIGN, false, T>(buf, TP, col, b, L, a.logL, tw, true, a.r3);
   };
   using FWD = std::integral_constant<int, -1>;
