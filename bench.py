@@ -234,16 +234,16 @@ KERNEL_SOURCES = {
 }
 NCU_CAPTURES = {
     "bscan_1024x2048": {
-        "ax_fused": {"sha": "fdaeb9fbdb9e66e7", "dram": 42398976, "table": 16809984,
-                     "smem_wavefronts": 7944518},
-        "lat_update": {"sha": "a7988f37beab21b4", "dram": 34291200, "table": 0,
-                       "smem_wavefronts": 2904397},
+        "ax_fused": {"sha": "551ee6401bbb5c52", "dram": 42627840, "table": 16809984,
+                     "smem_wavefronts": 6615850},
+        "lat_update": {"sha": "3429094234edf90b", "dram": 34413568, "table": 0,
+                       "smem_wavefronts": 2366270},
     },
     "volume_256x256x2048": {
-        # 128 x 128 x 2048 capture with the plan's Stolt table: 781,205,504 B and
-        # 137,649,680 wavefronts over 8,194 pairs
-        "ax_fused": {"sha": "fdaeb9fbdb9e66e7", "dram": 3124249984, "table": 545292288,
-                     "smem_wavefronts": 550497927},
+        # 128 x 128 x 2048 capture with the plan's Stolt table: 782,502,144 B and
+        # 116,308,840 wavefronts over 8,194 pairs
+        "ax_fused": {"sha": "551ee6401bbb5c52", "dram": 3129435594, "table": 545292288,
+                     "smem_wavefronts": 465150194},
     },
 }
 

@@ -438,6 +438,61 @@ __device__ __forceinline__ void inverse_and_store(const AxArgs<T>& A, cpair<T>* 
   }
 }
 
+// FP32 plans at K = 2048 and 4096 take the column-split radix-16 transforms
+// (fft_col16.cuh): three shared-memory passes per transform instead of four,
+// the same threads and registers; the forward ends, and the inverse starts,
+// in the layout of the interpolation and the scatter.
+template <typename T, int LOGK> __host__ __device__ constexpr bool ax_col16() {
+  return std::is_same<T, float>::value && LOGK >= 11;
+}
+
+template <typename T, int LOGK>
+__device__ __forceinline__ void ax_twiddles(cplx<T>* tw, const StoltConst& sc) {
+  if constexpr (ax_col16<T, LOGK>()) c16::build_twiddles<LOGK>(reinterpret_cast<float4*>(tw));
+  else build_twiddles<T>(tw, axial_K<LOGK>(sc), sc.logK);
+}
+
+// Y = the K-point e^{+} DFT of the pair's scaled, zero-padded columns
+template <typename T, int LOGK>
+__device__ __forceinline__ void ax_forward(const AxArgs<T>& A, cpair<T>* Y, const cplx<T>* tw,
+                                           int c1, int c2, bool two) {
+  if constexpr (ax_col16<T, LOGK>()) {
+    constexpr int nz = (1 << LOGK) / 2;
+    const int c = threadIdx.x & 1;
+    const cplx<T>* x = c == 0 ? A.in + size_t(c1) * nz : (two ? A.in + size_t(c2) * nz : nullptr);
+    c16::forward<LOGK>(reinterpret_cast<float2*>(Y), reinterpret_cast<const float2*>(x),
+                       reinterpret_cast<const float*>(A.tab.scale),
+                       reinterpret_cast<const float4*>(tw));
+  } else {
+    load_and_fft<T, LOGK>(A, Y, tw, c1, c2, two);
+  }
+}
+
+// The e^{-} DFT of Y, truncation to the nz kept rows, scaling, the columns'
+// output (G, or u_hat = eta_hat - G/L)
+template <typename T, int LOGK>
+__device__ __forceinline__ void ax_inverse(const AxArgs<T>& A, cpair<T>* Y, const cplx<T>* tw,
+                                           int c1, int c2, bool two) {
+  if constexpr (ax_col16<T, LOGK>()) {
+    // rows j + i K/16 of this thread's column; rows [K/4, 3K/4) are dropped
+    constexpr int K = 1 << LOGK, nz = K / 2, K16 = K / 16;
+    const int c = threadIdx.x & 1, jb = threadIdx.x >> 1;
+    const int col = c ? c2 : c1;
+    cplx<T>* o = A.out + size_t(col) * nz;
+    const bool keep = c == 0 || two;
+    c16::inverse<LOGK>(reinterpret_cast<float2*>(Y), reinterpret_cast<const float4*>(tw),
+                       [&](int i, const float2& y) {
+                         if (!keep || (i >= 4 && i < 12)) return;
+                         const int p = jb + i * K16;
+                         const int n = i < 4 ? p + nz / 2 : p - (K - nz / 2);
+                         put_output1(A, o, col, n, reinterpret_cast<const cplx<T>&>(y),
+                                     __ldg(A.tab.scale + n));
+                       });
+  } else {
+    inverse_and_store<T, LOGK>(A, Y, tw, c1, c2, two);
+  }
+}
+
 template <typename T, int J, int LOGK>
 __global__ void __launch_bounds__(512) k_ax_fwd(const __grid_constant__ AxArgs<T> A) {
   using C = cplx<T>;
@@ -450,8 +505,8 @@ __global__ void __launch_bounds__(512) k_ax_fwd(const __grid_constant__ AxArgs<T
   int c1, c2, mx, my;
   pair_columns(A, c1, c2, mx, my);
   const bool two = c2 != c1;
-  build_twiddles<T>(tw, K, sc.logK);
-  load_and_fft<T, LOGK>(A, Y, tw, c1, c2, two);
+  ax_twiddles<T, LOGK>(tw, sc);
+  ax_forward<T, LOGK>(A, Y, tw, c1, c2, two);
 
   const Positions<T> pos(A, mx, my);
   C* o1 = A.out + size_t(c1) * nk;
@@ -488,7 +543,7 @@ __global__ void __launch_bounds__(512, 2) k_ax_adj(const __grid_constant__ AxArg
   pair_columns(A, c1, c2, mx, my);
   const bool two = c2 != c1;
   if (tid == 0) { ch_lo = INT_MAX; ch_hi = INT_MIN; }
-  build_twiddles<T>(tw, K, sc.logK);
+  ax_twiddles<T, LOGK>(tw, sc);
   const Positions<T> pos(A, mx, my);
   const C* r1 = A.in + size_t(c1) * nk;
   const C* r2 = A.in + size_t(c2) * nk;
@@ -511,7 +566,7 @@ __global__ void __launch_bounds__(512, 2) k_ax_adj(const __grid_constant__ AxArg
   bool warp_tail;
   const int nch = prepare_scatter<T, J>(Y, K, nt, nk, sm, &ch_lo, &ch_hi, &ch_tail, warp_tail);
   scatter_samples<T, J>(A, Y, K, nt, sm, nch, warp_tail);
-  inverse_and_store<T, LOGK>(A, Y, tw, c1, c2, two);
+  ax_inverse<T, LOGK>(A, Y, tw, c1, c2, two);
 }
 
 // Forward model, data residual and adjoint of one column pair in one pass
@@ -538,14 +593,12 @@ __global__ void __launch_bounds__(512, 2) k_ax_fused(const __grid_constant__ AxA
   pair_columns(A, c1, c2, mx, my);
   const bool two = c2 != c1;
   if (tid == 0) { ch_lo = INT_MAX; ch_hi = INT_MIN; }
-  // FP32 at K = 2048, 4096: column-split radix-16 transforms (fft_col16.cuh)
-  constexpr bool COL16 = std::is_same<T, float>::value && LOGK >= 11;
+  constexpr bool COL16 = ax_col16<T, LOGK>();
   // Programmatic dependent launch: the next kernel in the stream may start its
   // own prologue on SMs this grid leaves idle; this grid builds its twiddles,
   // then waits for the previous kernel before touching global data.
   cudaTriggerProgrammaticLaunchCompletion();
-  if constexpr (COL16) c16::build_twiddles<(LOGK >= 11 ? LOGK : 11)>(reinterpret_cast<float4*>(tw));
-  else build_twiddles<T>(tw, K, sc.logK);
+  ax_twiddles<T, LOGK>(tw, sc);
   cudaGridDependencySynchronize();
   // F s_d at this pair's samples, fetched before the transforms need them (the
   // column-split transforms take them after the forward transform: their
@@ -559,20 +612,13 @@ __global__ void __launch_bounds__(512, 2) k_ax_fused(const __grid_constant__ AxA
       dqv[rho] = j < nk ? d1[j] : mk<T>(0, 0);
     }
   }
+  ax_forward<T, LOGK>(A, Y, tw, c1, c2, two);
   if constexpr (COL16) {
-    const int c = tid & 1;
-    const C* x = c == 0 ? A.in + size_t(c1) * (K / 2) : (two ? A.in + size_t(c2) * (K / 2) : nullptr);
-    c16::forward<(LOGK >= 11 ? LOGK : 11)>(reinterpret_cast<float2*>(Y),
-                                           reinterpret_cast<const float2*>(x),
-                                           reinterpret_cast<const float*>(A.tab.scale),
-                                           reinterpret_cast<const float4*>(tw));
 #pragma unroll
     for (int rho = 0; rho < NRES; ++rho) {
       const int j = NRES * tid + rho;
       dqv[rho] = j < nk ? d1[j] : mk<T>(0, 0);
     }
-  } else {
-    load_and_fft<T, LOGK>(A, Y, tw, c1, c2, two);
   }
 
   const Positions<T> pos(A, mx, my);
@@ -612,24 +658,7 @@ __global__ void __launch_bounds__(512, 2) k_ax_fused(const __grid_constant__ AxA
   bool warp_tail;
   const int nch = prepare_scatter<T, J>(Y, K, nt, nk, sm, &ch_lo, &ch_hi, &ch_tail, warp_tail);
   scatter_samples<T, J>(A, Y, K, nt, sm, nch, warp_tail);
-  if constexpr (COL16) {
-    // rows j + i K/16 of this thread's column; rows [K/4, 3K/4) are dropped
-    constexpr int KK = 1 << (LOGK >= 11 ? LOGK : 11), nz = KK / 2, K16 = KK / 16;
-    const int c = tid & 1, jb = tid >> 1;
-    const int col = c ? c2 : c1;
-    C* o = A.out + size_t(col) * nz;
-    const bool keep = c == 0 || two;
-    c16::inverse<(LOGK >= 11 ? LOGK : 11)>(
-        reinterpret_cast<float2*>(Y), reinterpret_cast<const float4*>(tw),
-        [&](int i, const float2& y) {
-          if (!keep || (i >= 4 && i < 12)) return;
-          const int p = jb + i * K16;
-          const int n = i < 4 ? p + nz / 2 : p - (KK - nz / 2);
-          put_output1(A, o, col, n, reinterpret_cast<const C&>(y), __ldg(A.tab.scale + n));
-        });
-  } else {
-    inverse_and_store<T, LOGK>(A, Y, tw, c1, c2, two);
-  }
+  ax_inverse<T, LOGK>(A, Y, tw, c1, c2, two);
 }
 
 // One thread per (|q| class, k_j): the same evaluation the kernels do on the fly.
