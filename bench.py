@@ -234,16 +234,16 @@ KERNEL_SOURCES = {
 }
 NCU_CAPTURES = {
     "bscan_1024x2048": {
-        "ax_fused": {"sha": "551ee6401bbb5c52", "dram": 42627840, "table": 16809984,
-                     "smem_wavefronts": 6615850},
-        "lat_update": {"sha": "3429094234edf90b", "dram": 34413568, "table": 0,
-                       "smem_wavefronts": 2366270},
+        "ax_fused": {"sha": "c4b631adffaf9283", "dram": 42434304, "table": 16809984,
+                     "smem_wavefronts": 6616636},
+        "lat_update": {"sha": "cd9416c519db2f3f", "dram": 34451200, "table": 0,
+                       "smem_wavefronts": 2375502},
     },
     "volume_256x256x2048": {
-        # 128 x 128 x 2048 capture with the plan's Stolt table: 782,502,144 B and
-        # 116,308,840 wavefronts over 8,194 pairs
-        "ax_fused": {"sha": "551ee6401bbb5c52", "dram": 3129435594, "table": 545292288,
-                     "smem_wavefronts": 465150194},
+        # 128 x 128 x 2048 capture with the plan's Stolt table: 782,257,152 B and
+        # 116,306,560 wavefronts over 8,194 pairs
+        "ax_fused": {"sha": "c4b631adffaf9283", "dram": 3128455806, "table": 545292288,
+                     "smem_wavefronts": 465141075},
     },
 }
 

@@ -320,18 +320,48 @@ int64_t isam_batch_kernel_count(const isam_batch* batch);
 isam_status isam_batch_entry_ms(const isam_batch* batch, double* ms);
 void isam_batch_destroy(isam_batch* batch);
 
-/* Pick launch shapes by timing the plan's own FISTA iteration (CUDA events on
- * the plan's stream, zero data, 10 timed iterations per candidate): the
- * lateral-update tile width (1, 2, 4 or 8 pairs of depth columns per block,
- * where they fit) and, when the plan holds a Stolt table, table lookups versus
- * on-the-fly Stolt positions.  Neither choice changes any column's arithmetic.
- * The fastest is kept in the plan and used by later calls; *tile and
- * *stolt_table (nullable) receive it.  Overwrites the plan's workspace.
- * When the environment variable ISAM_AUTOTUNE_CACHE names a file, a choice
- * recorded there for the same device, sizes, precision, J and table mode is
- * used without timing (if still feasible), and new choices are appended as
- * lines "<key> -> tile=<t> stolt=<m>".  Synchronous. */
+/* Launch shapes and FFT radices of a plan.  The paper has no counterpart (it
+ * states the method, not its kernels); none of these changes what is computed,
+ * only the order of rounding (the radices) or nothing at all (tile, table).
+ *   lateral_tile   pairs of depth columns per block of the lateral update: 1, 2,
+ *                  4 or 8 where they fit (threads = 8 x tile x L/8 <= 512, tile
+ *                  <= columns/2), 0 for the built-in choice (reported as used)
+ *   stolt_table    1: read the plan's table of Stolt positions and phases; 0:
+ *                  evaluate them in the kernels (the only mode without a table)
+ *   axial_radix    16: column-split radix-16 passes for the FP32 axial
+ *                  transforms at K = 2048 and 4096 (three shared-memory passes);
+ *                  8: radix-8 passes on column pairs (four); other plans run
+ *                  radix 8 whatever the value
+ *   lateral_radix  the same choice for the FP32 lateral tiles of L = 1024 (4
+ *                  pairs) and L = 256 (8 pairs) */
+typedef struct {
+  int32_t lateral_tile;
+  int32_t stolt_table;
+  int32_t axial_radix;
+  int32_t lateral_radix;
+} isam_tuning;
+
+/* Pick launch shapes and radices by timing the plan's own FISTA iteration
+ * (CUDA events on the plan's stream, zero data, 10 timed iterations per
+ * candidate): every feasible tile width, table versus evaluated positions when
+ * the plan holds a table, and radix 8 versus 16 where both forms exist.  The
+ * fastest is kept in the plan and used by later calls; *out (nullable)
+ * receives it.  Overwrites the plan's workspace.  When the environment
+ * variable ISAM_AUTOTUNE_CACHE names a file, a choice recorded there for the
+ * same device, sizes, precision, J and table mode is used without timing (if
+ * still feasible), and new choices are appended as lines
+ * "<key> -> tile=<t> stolt=<m> radix=<axial>/<lateral>".  ISAM_ERR_INVALID
+ * while a batch records the plan.  Synchronous. */
+isam_status isam_autotune_ex(isam_plan* plan, isam_tuning* out);
+/* isam_autotune_ex reporting the tile and the table mode only. */
 isam_status isam_autotune(isam_plan* plan, int32_t* tile, int32_t* stolt_table);
+/* The plan's current tuning (the built-in choices until tuned or set). */
+isam_status isam_get_tuning(const isam_plan* plan, isam_tuning* out);
+/* Install a tuning chosen elsewhere (offline, or to compare the forms):
+ * ISAM_ERR_INVALID for values out of range or a tile that does not fit,
+ * ISAM_ERR_UNSUPPORTED for stolt_table = 1 on a plan without a table, and
+ * ISAM_ERR_INVALID while a batch records the plan. */
+isam_status isam_set_tuning(isam_plan* plan, const isam_tuning* tuning);
 
 /* Kernel launches issued by the last isam_forward / isam_adjoint / isam_solve. */
 int64_t isam_last_launch_count(const isam_plan* plan);

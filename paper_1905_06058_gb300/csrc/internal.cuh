@@ -88,6 +88,9 @@ template <typename T> struct LatArgs {
   cplx<T>* uout;         // optional: u^k = eta^k - g^k before the threshold
   const double* lam_dev; // optional: lambda / L = lam_scale * (*lam_dev), read on the device
   double lam_scale;
+  // FP32 compile-time tiles at L = 1024 and 256: 1 runs the column-split
+  // radix-16 transforms, 0 the radix-8 column-pair ones; ignored elsewhere
+  int radix16;
 };
 
 // Columns q and -q share the Stolt map; the axial kernels process them as a
@@ -108,6 +111,9 @@ template <typename T> struct AxArgs {
   // fused kernel, optional: the model spectra S = phase . N(eta_hat)
   // ([ny][nx][nk], as k_ax_fwd writes them)
   cplx<T>* s_out;
+  // FP32, K = 2048 or 4096: 1 runs the column-split radix-16 transforms, 0 the
+  // radix-8 column-pair ones (the plan's tuned choice); ignored elsewhere
+  int radix16;
 };
 
 // launchers (return cudaGetLastError())

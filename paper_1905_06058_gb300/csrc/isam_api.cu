@@ -74,6 +74,11 @@ struct isam_plan {
   // and whether the fused kernel reads the Stolt table (1) or evaluates (2)
   int tune_tp = 0;
   int tune_table = 0;
+  // FFT radix of the FP32 axial transforms at K = 2048 / 4096 and of the
+  // compile-time lateral tiles at L = 1024 / 256: 16 (column-split radix-16
+  // passes, the default) or 8 (radix-8 column-pair passes)
+  int tune_radix_ax = 16;
+  int tune_radix_lat = 16;
   int batch_refs = 0;           // batches whose graph records this plan's kernels
   // filter B of Eq. 3 per |q| class, interleaved (re, im); empty: B = 1
   std::vector<double> filt_host;
@@ -323,7 +328,9 @@ LatArgs<T> lat_args(int B, int L, int M, const void* in, void* out) {
 template <typename T> isam_status lat(isam_plan* P, int mode, const LatArgs<T>& a) {
   const int cls = mode == LAT_UPDATE || mode == LAT_UPDATE_U ? ISAM_KCLASS_LAT_UPDATE
                                                              : ISAM_KCLASS_LAT_FFT;
-  return launch(P, cls, [&] { return launch_lat<T>(mode, a, P->stream); });
+  LatArgs<T> b = a;
+  b.radix16 = P->tune_radix_lat == 16 ? 1 : 0;
+  return launch(P, cls, [&] { return launch_lat<T>(mode, b, P->stream); });
 }
 
 template <typename T> const Poly<T>& poly_of(const isam_plan* P);
@@ -337,6 +344,7 @@ template <typename T> AxArgs<T> ax_args(isam_plan* P, const Impl<T>& im, const c
   a.poly = poly_of<T>(P);
   a.pairs = P->pairs;
   if (P->tune_table == 2) a.tab.stab = nullptr;
+  a.radix16 = P->tune_radix_ax == 16 ? 1 : 0;
   return a;
 }
 
@@ -1775,9 +1783,16 @@ std::string tune_key(const isam_plan* P, bool has_table) {
   return buf;
 }
 
+// One tuning of a plan: lateral tile (0: built-in), Stolt-table mode (0: the
+// plan's default, 1: table, 2: evaluated), FFT radices (8 or 16).
+struct Tuning {
+  int tp = 0, tab = 0, rax = 16, rlat = 16;
+};
+
 // Cached choice for `key` from the file named by ISAM_AUTOTUNE_CACHE: lines
-// "<key> -> tile=<t> stolt=<m>"; the last matching line wins.
-bool tune_cache_lookup(const std::string& key, int* tp, int* tab) {
+// "<key> -> tile=<t> stolt=<m> radix=<axial>/<lateral>" (lines without the
+// radices, from earlier builds, mean 16/16); the last matching line wins.
+bool tune_cache_lookup(const std::string& key, Tuning* out) {
   const char* path = getenv("ISAM_AUTOTUNE_CACHE");
   if (!path || !*path) return false;
   FILE* f = fopen(path, "r");
@@ -1787,10 +1802,15 @@ bool tune_cache_lookup(const std::string& key, int* tp, int* tab) {
   const std::string head = key + " -> ";
   while (fgets(line, sizeof(line), f)) {
     if (strncmp(line, head.c_str(), head.size()) != 0) continue;
-    int t = 0, m = 0;
-    if (sscanf(line + head.size(), "tile=%d stolt=%d", &t, &m) == 2) {
-      *tp = t;
-      *tab = m;
+    Tuning t;
+    int consumed = 0;
+    if (sscanf(line + head.size(), "tile=%d stolt=%d%n", &t.tp, &t.tab, &consumed) == 2) {
+      int ra = 16, rl = 16;
+      if (sscanf(line + head.size() + consumed, " radix=%d/%d", &ra, &rl) == 2) {
+        t.rax = ra;
+        t.rlat = rl;
+      }
+      *out = t;
       found = true;
     }
   }
@@ -1798,67 +1818,107 @@ bool tune_cache_lookup(const std::string& key, int* tp, int* tab) {
   return found;
 }
 
-void tune_cache_store(const std::string& key, int tp, int tab) {
+void tune_cache_store(const std::string& key, const Tuning& t) {
   const char* path = getenv("ISAM_AUTOTUNE_CACHE");
   if (!path || !*path) return;
   FILE* f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "%s -> tile=%d stolt=%d\n", key.c_str(), tp, tab);
+  fprintf(f, "%s -> tile=%d stolt=%d radix=%d/%d\n", key.c_str(), t.tp, t.tab, t.rax, t.rlat);
   fclose(f);
 }
 
-template <typename T> isam_status autotune_impl(isam_plan* P, int32_t* tile, int32_t* table) {
+// lateral extent and columns of the update pass (y for volumes)
+void update_geometry(const isam_plan* P, int* L, int* M) {
+  *L = P->ny == 1 ? P->nx : P->ny;
+  *M = P->ny == 1 ? P->nz : P->nx * P->nz;
+}
+
+template <typename T> bool tuning_feasible(const isam_plan* P, const Tuning& t) {
+  const Impl<T>& im = impl_of<T>(const_cast<isam_plan*>(P));
+  int L, M;
+  update_geometry(P, &L, &M);
+  const bool tile_ok = t.tp == 0 || ((t.tp == 1 || t.tp == 2 || t.tp == 4 || t.tp == 8) &&
+                                     t.tp <= M / 2 && (L >= 8 ? L / 8 : 1) * t.tp <= 512);
+  const bool tab_ok = t.tab == 0 || ((t.tab == 1 || t.tab == 2) && im.tab.stab);
+  const bool radix_ok = (t.rax == 8 || t.rax == 16) && (t.rlat == 8 || t.rlat == 16);
+  return tile_ok && tab_ok && radix_ok;
+}
+
+void apply_tuning(isam_plan* P, const Tuning& t) {
+  P->tune_tp = t.tp;
+  P->tune_table = t.tab;
+  P->tune_radix_ax = t.rax;
+  P->tune_radix_lat = t.rlat;
+}
+
+template <typename T> void report_tuning(const isam_plan* P, isam_tuning* out) {
+  const Impl<T>& im = impl_of<T>(const_cast<isam_plan*>(P));
+  int L, M;
+  update_geometry(P, &L, &M);
+  out->lateral_tile = P->tune_tp ? P->tune_tp : lat_tile(L, M);
+  out->stolt_table = P->tune_table == 2 ? 0 : (im.tab.stab ? 1 : 0);
+  out->axial_radix = P->tune_radix_ax;
+  out->lateral_radix = P->tune_radix_lat;
+}
+
+template <typename T> isam_status autotune_impl(isam_plan* P, isam_tuning* out) {
   Impl<T>& im = impl_of<T>(P);
+  const std::string key = tune_key(P, im.tab.stab != nullptr);
   {
     // a cached choice that is still feasible for this plan is used as is
-    const std::string key = tune_key(P, im.tab.stab != nullptr);
-    const int Lc = P->ny == 1 ? P->nx : P->ny;
-    const int Mc = P->ny == 1 ? P->nz : P->nx * P->nz;
-    int t = 0, m = 0;
-    if (tune_cache_lookup(key, &t, &m) && (t == 1 || t == 2 || t == 4 || t == 8) &&
-        t <= Mc / 2 && (Lc >= 8 ? Lc / 8 : 1) * t <= 512 &&
-        (m == 0 || ((m == 1 || m == 2) && im.tab.stab))) {
-      P->tune_tp = t;
-      P->tune_table = m;
-      if (tile) *tile = t;
-      if (table) *table = m == 2 ? 0 : (im.tab.stab ? 1 : 0);
+    Tuning t;
+    if (tune_cache_lookup(key, &t) && tuning_feasible<T>(P, t)) {
+      apply_tuning(P, t);
+      if (out) report_tuning<T>(P, out);
       return ISAM_OK;
     }
   }
   if (!im.zA) ISAM_TRY(dalloc(&im.zA, P->n_img));
   if (!im.zB) ISAM_TRY(dalloc(&im.zB, P->n_img));
   if (!im.sdh) ISAM_TRY(dalloc(&im.sdh, P->n_spec));
-  const int L = P->ny == 1 ? P->nx : P->ny;
-  const int M = P->ny == 1 ? P->nz : P->nx * P->nz;
+  int L, M;
+  update_geometry(P, &L, &M);
   const int threads_per_tp = L >= 8 ? L / 8 : 1;
+  const bool fp32 = P->p.precision == ISAM_FP32;
+  // radix-16 forms exist for FP32 axial transforms at K = 2048, 4096 and FP32
+  // lateral tiles (L, tile) = (1024, 4) and (256, 8) of lengths 2^p
+  const bool ax_both = fp32 && (P->K == 2048 || P->K == 4096);
   const bool prof = P->prof;
   P->prof = false;
   const int reps = 10;
   float best = 0.0f;
-  int best_tp = 0, best_tab = 0;
+  Tuning best_t;
+  bool have = false;
   const int tabs[2] = {1, 2};
   const int ntab = im.tab.stab ? 2 : 1;
   isam_status st = ISAM_OK;
   for (int it = 0; it < ntab && st == ISAM_OK; ++it) {
     for (int tp = 1; tp <= 8 && st == ISAM_OK; tp *= 2) {
       if (tp > M / 2 || threads_per_tp * tp > 512) continue;
-      P->tune_tp = tp;
-      P->tune_table = im.tab.stab ? tabs[it] : 0;
-      float ms = 0.0f;
-      st = time_iterations<T>(P, reps, &ms);
-      if (st == ISAM_OK && (best_tp == 0 || ms < best)) {
-        best = ms;
-        best_tp = tp;
-        best_tab = P->tune_table;
+      const bool lat_both = fp32 && ((L == 1024 && tp == 4) || (L == 256 && tp == 8));
+      for (int ra = ax_both ? 8 : 16; ra <= 16 && st == ISAM_OK; ra += 8) {
+        for (int rl = lat_both ? 8 : 16; rl <= 16 && st == ISAM_OK; rl += 8) {
+          Tuning t;
+          t.tp = tp;
+          t.tab = im.tab.stab ? tabs[it] : 0;
+          t.rax = ra;
+          t.rlat = rl;
+          apply_tuning(P, t);
+          float ms = 0.0f;
+          st = time_iterations<T>(P, reps, &ms);
+          if (st == ISAM_OK && (!have || ms < best)) {
+            best = ms;
+            best_t = t;
+            have = true;
+          }
+        }
       }
     }
   }
   P->prof = prof;
-  P->tune_tp = st == ISAM_OK ? best_tp : 0;
-  P->tune_table = st == ISAM_OK ? best_tab : 0;
-  if (st == ISAM_OK) tune_cache_store(tune_key(P, im.tab.stab != nullptr), best_tp, best_tab);
-  if (tile) *tile = P->tune_tp;
-  if (table) *table = P->tune_table == 2 ? 0 : (im.tab.stab ? 1 : 0);
+  apply_tuning(P, st == ISAM_OK ? best_t : Tuning());
+  if (st == ISAM_OK) tune_cache_store(key, best_t);
+  if (out) report_tuning<T>(P, out);
   return st;
 }
 
@@ -1866,13 +1926,47 @@ template <typename T> isam_status autotune_impl(isam_plan* P, int32_t* tile, int
 
 extern "C" {
 
-isam_status isam_autotune(isam_plan* P, int32_t* tile, int32_t* stolt_table) {
+isam_status isam_autotune_ex(isam_plan* P, isam_tuning* out) {
   if (!P) return ISAM_ERR_INVALID;
   if (P->batch_refs) return ISAM_ERR_INVALID;       // a batch graph records the plan
   DeviceGuard g(P->device);
   P->launches = 0;
-  if (P->p.precision == ISAM_FP64) return autotune_impl<double>(P, tile, stolt_table);
-  return autotune_impl<float>(P, tile, stolt_table);
+  if (P->p.precision == ISAM_FP64) return autotune_impl<double>(P, out);
+  return autotune_impl<float>(P, out);
+}
+
+isam_status isam_autotune(isam_plan* P, int32_t* tile, int32_t* stolt_table) {
+  isam_tuning t{};
+  const isam_status st = isam_autotune_ex(P, &t);
+  if (tile) *tile = t.lateral_tile;
+  if (stolt_table) *stolt_table = t.stolt_table;
+  return st;
+}
+
+isam_status isam_get_tuning(const isam_plan* P, isam_tuning* out) {
+  if (!P || !out) return ISAM_ERR_INVALID;
+  if (P->p.precision == ISAM_FP64) report_tuning<double>(P, out);
+  else report_tuning<float>(P, out);
+  return ISAM_OK;
+}
+
+isam_status isam_set_tuning(isam_plan* P, const isam_tuning* in) {
+  if (!P || !in) return ISAM_ERR_INVALID;
+  if (P->batch_refs) return ISAM_ERR_INVALID;
+  const bool has_table = P->p.precision == ISAM_FP64 ? P->f64.tab.stab != nullptr
+                                                      : P->f32.tab.stab != nullptr;
+  if (in->stolt_table != 0 && in->stolt_table != 1) return ISAM_ERR_INVALID;
+  if (in->stolt_table == 1 && !has_table) return ISAM_ERR_UNSUPPORTED;
+  Tuning t;
+  t.tp = in->lateral_tile;
+  t.tab = in->stolt_table == 1 ? 1 : (has_table ? 2 : 0);
+  t.rax = in->axial_radix;
+  t.rlat = in->lateral_radix;
+  const bool ok = P->p.precision == ISAM_FP64 ? tuning_feasible<double>(P, t)
+                                              : tuning_feasible<float>(P, t);
+  if (!ok) return ISAM_ERR_INVALID;
+  apply_tuning(P, t);
+  return ISAM_OK;
 }
 
 }  // extern "C"

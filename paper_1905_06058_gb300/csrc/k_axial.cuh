@@ -438,25 +438,29 @@ __device__ __forceinline__ void inverse_and_store(const AxArgs<T>& A, cpair<T>* 
   }
 }
 
-// FP32 plans at K = 2048 and 4096 take the column-split radix-16 transforms
-// (fft_col16.cuh): three shared-memory passes per transform instead of four,
-// the same threads and registers; the forward ends, and the inverse starts,
-// in the layout of the interpolation and the scatter.
-template <typename T, int LOGK> __host__ __device__ constexpr bool ax_col16() {
+// FP32 plans at K = 2048 and 4096 can take the column-split radix-16
+// transforms (fft_col16.cuh): three shared-memory passes per transform instead
+// of four, the same threads and registers; the forward ends, and the inverse
+// starts, in the layout of the interpolation and the scatter.  C16 selects
+// them (the plan's choice, AxArgs::radix16); other instances ignore it.
+template <typename T, int LOGK> __host__ __device__ constexpr bool ax_col16_exists() {
   return std::is_same<T, float>::value && LOGK >= 11;
 }
+template <typename T, int LOGK, bool C16> __host__ __device__ constexpr bool ax_col16() {
+  return C16 && ax_col16_exists<T, LOGK>();
+}
 
-template <typename T, int LOGK>
+template <typename T, int LOGK, bool C16>
 __device__ __forceinline__ void ax_twiddles(cplx<T>* tw, const StoltConst& sc) {
-  if constexpr (ax_col16<T, LOGK>()) c16::build_twiddles<LOGK>(reinterpret_cast<float4*>(tw));
+  if constexpr (ax_col16<T, LOGK, C16>()) c16::build_twiddles<LOGK>(reinterpret_cast<float4*>(tw));
   else build_twiddles<T>(tw, axial_K<LOGK>(sc), sc.logK);
 }
 
 // Y = the K-point e^{+} DFT of the pair's scaled, zero-padded columns
-template <typename T, int LOGK>
+template <typename T, int LOGK, bool C16>
 __device__ __forceinline__ void ax_forward(const AxArgs<T>& A, cpair<T>* Y, const cplx<T>* tw,
                                            int c1, int c2, bool two) {
-  if constexpr (ax_col16<T, LOGK>()) {
+  if constexpr (ax_col16<T, LOGK, C16>()) {
     constexpr int nz = (1 << LOGK) / 2;
     const int c = threadIdx.x & 1;
     const cplx<T>* x = c == 0 ? A.in + size_t(c1) * nz : (two ? A.in + size_t(c2) * nz : nullptr);
@@ -470,10 +474,10 @@ __device__ __forceinline__ void ax_forward(const AxArgs<T>& A, cpair<T>* Y, cons
 
 // The e^{-} DFT of Y, truncation to the nz kept rows, scaling, the columns'
 // output (G, or u_hat = eta_hat - G/L)
-template <typename T, int LOGK>
+template <typename T, int LOGK, bool C16>
 __device__ __forceinline__ void ax_inverse(const AxArgs<T>& A, cpair<T>* Y, const cplx<T>* tw,
                                            int c1, int c2, bool two) {
-  if constexpr (ax_col16<T, LOGK>()) {
+  if constexpr (ax_col16<T, LOGK, C16>()) {
     // rows j + i K/16 of this thread's column; rows [K/4, 3K/4) are dropped
     constexpr int K = 1 << LOGK, nz = K / 2, K16 = K / 16;
     const int c = threadIdx.x & 1, jb = threadIdx.x >> 1;
@@ -493,7 +497,7 @@ __device__ __forceinline__ void ax_inverse(const AxArgs<T>& A, cpair<T>* Y, cons
   }
 }
 
-template <typename T, int J, int LOGK>
+template <typename T, int J, int LOGK, bool C16>
 __global__ void __launch_bounds__(512) k_ax_fwd(const __grid_constant__ AxArgs<T> A) {
   using C = cplx<T>;
   using V = cpair<T>;
@@ -505,8 +509,8 @@ __global__ void __launch_bounds__(512) k_ax_fwd(const __grid_constant__ AxArgs<T
   int c1, c2, mx, my;
   pair_columns(A, c1, c2, mx, my);
   const bool two = c2 != c1;
-  ax_twiddles<T, LOGK>(tw, sc);
-  ax_forward<T, LOGK>(A, Y, tw, c1, c2, two);
+  ax_twiddles<T, LOGK, C16>(tw, sc);
+  ax_forward<T, LOGK, C16>(A, Y, tw, c1, c2, two);
 
   const Positions<T> pos(A, mx, my);
   C* o1 = A.out + size_t(c1) * nk;
@@ -528,7 +532,7 @@ __global__ void __launch_bounds__(512) k_ax_fwd(const __grid_constant__ AxArgs<T
   }
 }
 
-template <typename T, int J, int LOGK>
+template <typename T, int J, int LOGK, bool C16>
 __global__ void __launch_bounds__(512, 2) k_ax_adj(const __grid_constant__ AxArgs<T> A) {
   using C = cplx<T>;
   using V = cpair<T>;
@@ -543,7 +547,7 @@ __global__ void __launch_bounds__(512, 2) k_ax_adj(const __grid_constant__ AxArg
   pair_columns(A, c1, c2, mx, my);
   const bool two = c2 != c1;
   if (tid == 0) { ch_lo = INT_MAX; ch_hi = INT_MIN; }
-  ax_twiddles<T, LOGK>(tw, sc);
+  ax_twiddles<T, LOGK, C16>(tw, sc);
   const Positions<T> pos(A, mx, my);
   const C* r1 = A.in + size_t(c1) * nk;
   const C* r2 = A.in + size_t(c2) * nk;
@@ -566,7 +570,7 @@ __global__ void __launch_bounds__(512, 2) k_ax_adj(const __grid_constant__ AxArg
   bool warp_tail;
   const int nch = prepare_scatter<T, J>(Y, K, nt, nk, sm, &ch_lo, &ch_hi, &ch_tail, warp_tail);
   scatter_samples<T, J>(A, Y, K, nt, sm, nch, warp_tail);
-  ax_inverse<T, LOGK>(A, Y, tw, c1, c2, two);
+  ax_inverse<T, LOGK, C16>(A, Y, tw, c1, c2, two);
 }
 
 // Forward model, data residual and adjoint of one column pair in one pass
@@ -578,7 +582,7 @@ __global__ void __launch_bounds__(512, 2) k_ax_adj(const __grid_constant__ AxArg
 // u_hat_scale = 1/L, as u_hat = eta_hat - G/L (put_output).  F s_d is
 // Hermitian, so only its c1 column is read.
 // WS: also write the model spectra S to A.s_out.
-template <typename T, int J, int LOGK, bool WS>
+template <typename T, int J, int LOGK, bool WS, bool C16>
 __global__ void __launch_bounds__(512, 2) k_ax_fused(const __grid_constant__ AxArgs<T> A) {
   using C = cplx<T>;
   using V = cpair<T>;
@@ -593,12 +597,12 @@ __global__ void __launch_bounds__(512, 2) k_ax_fused(const __grid_constant__ AxA
   pair_columns(A, c1, c2, mx, my);
   const bool two = c2 != c1;
   if (tid == 0) { ch_lo = INT_MAX; ch_hi = INT_MIN; }
-  constexpr bool COL16 = ax_col16<T, LOGK>();
+  constexpr bool COL16 = ax_col16<T, LOGK, C16>();
   // Programmatic dependent launch: the next kernel in the stream may start its
   // own prologue on SMs this grid leaves idle; this grid builds its twiddles,
   // then waits for the previous kernel before touching global data.
   cudaTriggerProgrammaticLaunchCompletion();
-  ax_twiddles<T, LOGK>(tw, sc);
+  ax_twiddles<T, LOGK, C16>(tw, sc);
   cudaGridDependencySynchronize();
   // F s_d at this pair's samples, fetched before the transforms need them (the
   // column-split transforms take them after the forward transform: their
@@ -612,7 +616,7 @@ __global__ void __launch_bounds__(512, 2) k_ax_fused(const __grid_constant__ AxA
       dqv[rho] = j < nk ? d1[j] : mk<T>(0, 0);
     }
   }
-  ax_forward<T, LOGK>(A, Y, tw, c1, c2, two);
+  ax_forward<T, LOGK, C16>(A, Y, tw, c1, c2, two);
   if constexpr (COL16) {
 #pragma unroll
     for (int rho = 0; rho < NRES; ++rho) {
@@ -658,7 +662,7 @@ __global__ void __launch_bounds__(512, 2) k_ax_fused(const __grid_constant__ AxA
   bool warp_tail;
   const int nch = prepare_scatter<T, J>(Y, K, nt, nk, sm, &ch_lo, &ch_hi, &ch_tail, warp_tail);
   scatter_samples<T, J>(A, Y, K, nt, sm, nch, warp_tail);
-  ax_inverse<T, LOGK>(A, Y, tw, c1, c2, two);
+  ax_inverse<T, LOGK, C16>(A, Y, tw, c1, c2, two);
 }
 
 // One thread per (|q| class, k_j): the same evaluation the kernels do on the fly.
@@ -702,19 +706,21 @@ template <typename T> size_t ax_smem_bytes(int K, int nk, bool adj) {
 
 enum { AX_FWD = 0, AX_ADJ = 1, AX_FUSED = 2 };
 
-template <typename T, int J, int LOGK>
-static cudaError_t launch_ax_JK(const AxArgs<T>& a, int npairs, cudaStream_t s, int kind) {
+template <typename T, int J, int LOGK, bool C16>
+static cudaError_t launch_ax_JKC(const AxArgs<T>& a, int npairs, cudaStream_t s, int kind) {
   const int K = a.sc.K;
   const int threads = K / 8;
   const size_t sm = ax_smem_bytes<T>(K, a.sc.nk, kind != AX_FWD);
   if (kind == AX_ADJ) {
-    cudaFuncSetAttribute(k_ax_adj<T, J, LOGK>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-    k_ax_adj<T, J, LOGK><<<npairs, threads, sm, s>>>(a);
+    auto* kern = k_ax_adj<T, J, LOGK, C16>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    kern<<<npairs, threads, sm, s>>>(a);
   } else if (kind == AX_FWD) {
-    cudaFuncSetAttribute(k_ax_fwd<T, J, LOGK>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-    k_ax_fwd<T, J, LOGK><<<npairs, threads, sm, s>>>(a);
+    auto* kern = k_ax_fwd<T, J, LOGK, C16>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    kern<<<npairs, threads, sm, s>>>(a);
   } else {
-    auto* kern = a.s_out ? k_ax_fused<T, J, LOGK, true> : k_ax_fused<T, J, LOGK, false>;
+    auto* kern = a.s_out ? k_ax_fused<T, J, LOGK, true, C16> : k_ax_fused<T, J, LOGK, false, C16>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
     // programmatic dependent launch (see k_ax_fused's prologue)
     cudaLaunchConfig_t cfg = {};
@@ -730,6 +736,15 @@ static cudaError_t launch_ax_JK(const AxArgs<T>& a, int npairs, cudaStream_t s, 
     return cudaLaunchKernelEx(&cfg, kern, a);
   }
   return cudaGetLastError();
+}
+
+// the plan's radix choice (a.radix16) where both forms exist
+template <typename T, int J, int LOGK>
+static cudaError_t launch_ax_JK(const AxArgs<T>& a, int npairs, cudaStream_t s, int kind) {
+  if constexpr (ax_col16_exists<T, LOGK>()) {
+    if (a.radix16) return launch_ax_JKC<T, J, LOGK, true>(a, npairs, s, kind);
+  }
+  return launch_ax_JKC<T, J, LOGK, false>(a, npairs, s, kind);
 }
 
 // K = 4096 and 2048 (nz = 2048, 1024) run the compile-time-length instances

@@ -81,7 +81,7 @@ template <> struct rpair_t<double> { using type = double2; };
 // LOGL > 0: the transforms are the compile-time-length ones for L = 2^LOGL at
 // the stride 2^LOGTP = TP (no radix-3 pass), with constant row offsets;
 // LOGL = 0: runtime-length transforms.  The tile indexing is the same.
-template <typename T, int MODE, int LOGL, int LOGTP>
+template <typename T, int MODE, int LOGL, int LOGTP, bool C16>
 __global__ void __launch_bounds__(512, 2) k_lat(const __grid_constant__ LatArgs<T> a) {
   using C = cplx<T>;
   using V = cpair<T>;
@@ -93,7 +93,8 @@ __global__ void __launch_bounds__(512, 2) k_lat(const __grid_constant__ LatArgs<
   const int TP = a.TZ, L = CT ? (1 << LOGL) : a.L, logTP = a.logTZ;
   cplx<T>* tw = reinterpret_cast<cplx<T>*>(buf + size_t(padded_rows(L)) * TP);
   // FP32 at L = 1024 and 256: column-split radix-16 transforms (fft_col16.cuh)
-  constexpr bool COL16 = CT && std::is_same<T, float>::value && (LOGL == 10 || LOGL == 8);
+  // when the plan chose them (C16)
+  constexpr bool COL16 = C16 && CT && std::is_same<T, float>::value && (LOGL == 10 || LOGL == 8);
   // programmatic dependent launch: let the next kernel start its prologue,
   // build the twiddles, then wait for the previous kernel's results
   cudaTriggerProgrammaticLaunchCompletion();
@@ -349,11 +350,11 @@ template <typename T> size_t lat_smem_bytes(int L, int TP) {
          size_t(twiddle_entries(L, lg, r3)) * sizeof(cplx<T>);
 }
 
-template <typename T, int MODE, int LOGL, int LOGTP>
+template <typename T, int MODE, int LOGL, int LOGTP, bool C16 = false>
 static cudaError_t launch_lat_tile(const LatArgs<T>& a, cudaStream_t s) {
   const int threads = (a.L >= 8 ? a.L / 8 : 1) * a.TZ;
   const size_t sm = lat_smem_bytes<T>(a.L, a.TZ);
-  auto* kern = k_lat<T, MODE, LOGL, LOGTP>;
+  auto* kern = k_lat<T, MODE, LOGL, LOGTP, C16>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
   dim3 grid(a.M / (2 * a.TZ), a.B);
   cudaLaunchConfig_t cfg = {};
@@ -371,17 +372,22 @@ static cudaError_t launch_lat_tile(const LatArgs<T>& a, cudaStream_t s) {
 
 // The FP32 solve passes at the tiles of the 1024-wide B-scans (L = 1024, 4
 // pair-columns), the 512-wide ones and the 256 x 256 volumes (L = 512 or 256, 8
-// pair-columns) run compile-time-length transforms; every other case the
-// runtime-length ones.
+// pair-columns) run compile-time-length transforms, at L = 1024 and 256 in the
+// column-split radix-16 form when the plan chose it (a.radix16); every other
+// case the runtime-length ones.
 template <typename T, int MODE>
 static cudaError_t launch_lat_mode(const LatArgs<T>& a, cudaStream_t s) {
   constexpr bool hot = std::is_same<T, float>::value &&
                        (MODE == LAT_UPDATE || MODE == LAT_UPDATE_U || MODE == LAT_C2C_FWD ||
                         MODE == LAT_C2C_INV);
   if constexpr (hot) {
-    if (!a.r3 && a.L == 1024 && a.TZ == 4) return launch_lat_tile<T, MODE, 10, 2>(a, s);
+    if (!a.r3 && a.L == 1024 && a.TZ == 4)
+      return a.radix16 ? launch_lat_tile<T, MODE, 10, 2, true>(a, s)
+                       : launch_lat_tile<T, MODE, 10, 2>(a, s);
     if (!a.r3 && a.L == 512 && a.TZ == 8) return launch_lat_tile<T, MODE, 9, 3>(a, s);
-    if (!a.r3 && a.L == 256 && a.TZ == 8) return launch_lat_tile<T, MODE, 8, 3>(a, s);
+    if (!a.r3 && a.L == 256 && a.TZ == 8)
+      return a.radix16 ? launch_lat_tile<T, MODE, 8, 3, true>(a, s)
+                       : launch_lat_tile<T, MODE, 8, 3>(a, s);
   }
   return launch_lat_tile<T, MODE, 0, 0>(a, s);
 }

@@ -61,6 +61,11 @@ class SolveInfo(ctypes.Structure):
                 ("objective", ctypes.c_double)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("lateral_tile", ctypes.c_int32), ("stolt_table", ctypes.c_int32),
+                ("axial_radix", ctypes.c_int32), ("lateral_radix", ctypes.c_int32)]
+
+
 _P = ctypes.c_void_p
 _ALLOC_T = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 _FREE_T = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
@@ -90,6 +95,9 @@ _SIGS = {
     "isam_batch_run": (ctypes.c_int, [_P, ctypes.POINTER(SolveInfo)]),
     "isam_autotune": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32),
                                      ctypes.POINTER(ctypes.c_int32)]),
+    "isam_autotune_ex": (ctypes.c_int, [_P, ctypes.POINTER(Tuning)]),
+    "isam_get_tuning": (ctypes.c_int, [_P, ctypes.POINTER(Tuning)]),
+    "isam_set_tuning": (ctypes.c_int, [_P, ctypes.POINTER(Tuning)]),
     "isam_batch_kernel_count": (ctypes.c_int64, [_P]),
     "isam_data_fidelity": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
     "isam_batch_entry_ms": (ctypes.c_int, [_P, _P]),
@@ -436,13 +444,34 @@ class Plan:
             None if sb is None else _P(sb.data_ptr()), g), "isam_fista_unrolled_vjp")
         return np.array(g[:], dtype=np.float64), sb
 
+    @staticmethod
+    def _tuning_dict(t: "Tuning") -> dict:
+        return {"lateral_tile": t.lateral_tile, "stolt_table": bool(t.stolt_table),
+                "axial_radix": t.axial_radix, "lateral_radix": t.lateral_radix}
+
     def autotune(self) -> dict:
-        """isam_autotune: time the plan's own iteration and keep the fastest shapes."""
+        """isam_autotune_ex: time the plan's own iteration over the feasible tiles,
+        table modes and FFT radices, and keep the fastest."""
         self._sync_stream()
-        tile, tab = ctypes.c_int32(), ctypes.c_int32()
-        _check(_lib.isam_autotune(self._h, ctypes.byref(tile), ctypes.byref(tab)),
-               "isam_autotune")
-        return {"lateral_tile": tile.value, "stolt_table": bool(tab.value)}
+        t = Tuning()
+        _check(_lib.isam_autotune_ex(self._h, ctypes.byref(t)), "isam_autotune_ex")
+        return self._tuning_dict(t)
+
+    def tuning(self) -> dict:
+        """isam_get_tuning: the launch shapes and radices the plan uses."""
+        t = Tuning()
+        _check(_lib.isam_get_tuning(self._h, ctypes.byref(t)), "isam_get_tuning")
+        return self._tuning_dict(t)
+
+    def set_tuning(self, lateral_tile=0, stolt_table=None, axial_radix=16,
+                   lateral_radix=16) -> None:
+        """isam_set_tuning; stolt_table None keeps the table when the plan has one."""
+        self._sync_stream()
+        if stolt_table is None:
+            stolt_table = self.tuning()["stolt_table"]
+        t = Tuning(int(lateral_tile), int(bool(stolt_table)), int(axial_radix),
+                   int(lateral_radix))
+        _check(_lib.isam_set_tuning(self._h, ctypes.byref(t)), "isam_set_tuning")
 
     def max_abs(self, eta) -> float:
         self._sync_stream()

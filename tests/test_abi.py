@@ -50,6 +50,8 @@ int main(void) {
   printf("isam_solve_opts %zu\n", sizeof(isam_solve_opts));
   printf("isam_solve_state %zu\n", sizeof(isam_solve_state));
   printf("isam_solve_info %zu\n", sizeof(isam_solve_info));
+  printf("isam_tuning %zu\n", sizeof(isam_tuning));
+  P(isam_tuning, stolt_table) P(isam_tuning, lateral_radix)
   P(isam_params, k_min) P(isam_params, dx) P(isam_params, z0) P(isam_params, n_disp)
   P(isam_params, disp) P(isam_params, precision) P(isam_params, nufft_os)
   P(isam_params, flags)
@@ -68,7 +70,8 @@ int main(void) {
         lines = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split("\n")
     got = dict(line.rsplit(" ", 1) for line in lines if line)
     types = {"isam_params": isam.IsamParams, "isam_solve_opts": isam.SolveOpts,
-             "isam_solve_state": isam.SolveState, "isam_solve_info": isam.SolveInfo}
+             "isam_solve_state": isam.SolveState, "isam_solve_info": isam.SolveInfo,
+             "isam_tuning": isam.Tuning}
     for key, val in got.items():
         if "." in key:
             t, f = key.split(".")
@@ -130,6 +133,9 @@ def test_null_arguments(isam):
     assert lib.isam_batch_create(None, 0, None, None, None, None, None) == 1
     assert lib.isam_batch_entry_ms(None, None) == 1
     assert lib.isam_data_fidelity(None, None, None, None, None) == 1
+    assert lib.isam_autotune_ex(None, None) == 1
+    assert lib.isam_get_tuning(None, None) == 1
+    assert lib.isam_set_tuning(None, None) == 1
     assert lib.isam_set_filter(None, None) == 1
     assert lib.isam_unrolled_checkpoint_images(20, 5) == 8
     assert lib.isam_unrolled_checkpoint_images(0, 5) == -1

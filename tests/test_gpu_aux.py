@@ -118,7 +118,9 @@ def test_autotune_cache_file(torch, tmp_path):
         with open(path, "a") as f:                          # a later entry wins
             f.write(f"{key} -> tile=1 stolt=2\n")
         p3 = Plan(g)
-        assert p3.autotune() == {"lateral_tile": 1, "stolt_table": False}
+        # (a line without radices, as earlier builds wrote them, means 16/16)
+        assert p3.autotune() == {"lateral_tile": 1, "stolt_table": False, "axial_radix": 16,
+                                 "lateral_radix": 16}
         for p in (p1, p2, p3):
             p.close()
     finally:
