@@ -17,6 +17,22 @@ template <typename T> __host__ __device__ __forceinline__ cplx<T> mk(T re, T im)
 }
 template <typename C> __host__ __device__ __forceinline__ C cadd(C a, C b) { a.x += b.x; a.y += b.y; return a; }
 template <typename C> __host__ __device__ __forceinline__ C csub(C a, C b) { a.x -= b.x; a.y -= b.y; return a; }
+// FP32: one packed two-lane instruction on sm_100 and later, each lane rounded
+// to nearest like the scalar form (so the results are the same bits)
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+  return __fadd2_rn(a, b);
+#else
+  a.x += b.x; a.y += b.y; return a;
+#endif
+}
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+  return __fadd2_rn(a, make_float2(-b.x, -b.y));
+#else
+  a.x -= b.x; a.y -= b.y; return a;
+#endif
+}
 template <typename C> __host__ __device__ __forceinline__ C cmul(C a, C b) {
   C r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
 }
@@ -26,6 +42,17 @@ template <typename C> __host__ __device__ __forceinline__ C cmulc(C a, C b) {
 }
 template <typename C, typename T> __host__ __device__ __forceinline__ C cscale(C a, T s) { a.x *= s; a.y *= s; return a; }
 template <typename C> __host__ __device__ __forceinline__ C cconj(C a) { a.y = -a.y; return a; }
+// acc + c y for a real c
+template <typename C, typename T> __device__ __forceinline__ C cfma_r(T c, C y, C acc) {
+  acc.x = fma(c, y.x, acc.x); acc.y = fma(c, y.y, acc.y); return acc;
+}
+__device__ __forceinline__ float2 cfma_r(float c, float2 y, float2 acc) {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+  return __ffma2_rn(make_float2(c, c), y, acc);
+#else
+  acc.x = fmaf(c, y.x, acc.x); acc.y = fmaf(c, y.y, acc.y); return acc;
+#endif
+}
 // multiply by sign * i   (sign = +1 or -1)
 template <int SIGN, typename C> __host__ __device__ __forceinline__ C cmul_i(C a) {
   C r; r.x = -SIGN * a.y; r.y = SIGN * a.x; return r;

@@ -52,11 +52,10 @@ __device__ __forceinline__ void dft16(float2* a) {
   for (int n2 = 0; n2 < 4; ++n2) {
     if (HALF_ZERO) {
       const float2 x0 = a[n2], x3 = a[n2 + 12];
-      const float2 ix3 = cmul_i<SIGN>(x3);
       b[n2][0] = cadd(x0, x3);
-      b[n2][1] = csub(x0, ix3);
+      b[n2][1] = sub_rot<SIGN>(x0, x3);
       b[n2][2] = csub(x0, x3);
-      b[n2][3] = cadd(x0, ix3);
+      b[n2][3] = add_rot<SIGN>(x0, x3);
     } else {
       float2 x0 = a[n2], x1 = a[n2 + 4], x2 = a[n2 + 8], x3 = a[n2 + 12];
       dft4<SIGN>(x0, x1, x2, x3);

@@ -60,6 +60,21 @@ template <int SIGN, typename T> __device__ __forceinline__ cpair<T> ew8_3(cpair<
   return {ew8_3<SIGN>(o.a), ew8_3<SIGN>(o.b)};
 }
 
+// t + SIGN i s and t - SIGN i s, lane by lane (no operand swap for the
+// packed two-lane adds of the FP32 forms)
+template <int SIGN, typename C> __device__ __forceinline__ C add_rot(C t, C s) {
+  C r; r.x = t.x - SIGN * s.y; r.y = t.y + SIGN * s.x; return r;
+}
+template <int SIGN, typename C> __device__ __forceinline__ C sub_rot(C t, C s) {
+  C r; r.x = t.x + SIGN * s.y; r.y = t.y - SIGN * s.x; return r;
+}
+template <int SIGN, typename T> __device__ __forceinline__ cpair<T> add_rot(cpair<T> t, cpair<T> s) {
+  return {add_rot<SIGN>(t.a, s.a), add_rot<SIGN>(t.b, s.b)};
+}
+template <int SIGN, typename T> __device__ __forceinline__ cpair<T> sub_rot(cpair<T> t, cpair<T> s) {
+  return {sub_rot<SIGN>(t.a, s.a), sub_rot<SIGN>(t.b, s.b)};
+}
+
 template <int SIGN, typename E>
 __device__ __forceinline__ void dft2(E& a, E& b) {
   E t = a; a = eadd(t, b); b = esub(t, b);
@@ -68,9 +83,9 @@ __device__ __forceinline__ void dft2(E& a, E& b) {
 template <int SIGN, typename E>
 __device__ __forceinline__ void dft4(E& a0, E& a1, E& a2, E& a3) {
   E t0 = eadd(a0, a2), t1 = esub(a0, a2);
-  E t2 = eadd(a1, a3), t3 = emul_i<SIGN>(esub(a1, a3));
+  E t2 = eadd(a1, a3), t3 = esub(a1, a3);
   a0 = eadd(t0, t2); a2 = esub(t0, t2);
-  a1 = eadd(t1, t3); a3 = esub(t1, t3);
+  a1 = add_rot<SIGN>(t1, t3); a3 = sub_rot<SIGN>(t1, t3);
 }
 
 template <int SIGN, bool HALF_ZERO = false, typename E>
@@ -78,16 +93,13 @@ __device__ __forceinline__ void dft8(E* a) {
   if (HALF_ZERO) {
     // a[2..5] == 0: even part (a0, 0, 0, a6), odd part (a1, 0, 0, a7)
     const E e0 = eadd(a[0], a[6]), e2 = esub(a[0], a[6]);
-    const E i6 = emul_i<SIGN>(a[6]);
-    const E e1 = esub(a[0], i6), e3 = eadd(a[0], i6);
+    const E e1 = sub_rot<SIGN>(a[0], a[6]), e3 = add_rot<SIGN>(a[0], a[6]);
     const E o0 = eadd(a[1], a[7]), o2 = esub(a[1], a[7]);
-    const E i7 = emul_i<SIGN>(a[7]);
-    const E o1 = ew8_1<SIGN>(esub(a[1], i7));
-    const E o2w = emul_i<SIGN>(o2);
-    const E o3 = ew8_3<SIGN>(eadd(a[1], i7));
+    const E o1 = ew8_1<SIGN>(sub_rot<SIGN>(a[1], a[7]));
+    const E o3 = ew8_3<SIGN>(add_rot<SIGN>(a[1], a[7]));
     a[0] = eadd(e0, o0); a[4] = esub(e0, o0);
     a[1] = eadd(e1, o1); a[5] = esub(e1, o1);
-    a[2] = eadd(e2, o2w); a[6] = esub(e2, o2w);
+    a[2] = add_rot<SIGN>(e2, o2); a[6] = sub_rot<SIGN>(e2, o2);
     a[3] = eadd(e3, o3); a[7] = esub(e3, o3);
     return;
   }
@@ -95,14 +107,13 @@ __device__ __forceinline__ void dft8(E* a) {
   dft4<SIGN>(a[1], a[3], a[5], a[7]);
   // odd half times W8^k, W8 = e^{SIGN 2 pi i / 8}
   a[3] = ew8_1<SIGN>(a[3]);
-  a[5] = emul_i<SIGN>(a[5]);
   a[7] = ew8_3<SIGN>(a[7]);
-  // combine: y_k = E_k + W^k O_k, y_{k+4} = E_k - W^k O_k
+  // combine: y_k = E_k + W^k O_k, y_{k+4} = E_k - W^k O_k (W^2 = SIGN i)
   E e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6];
   E p0 = a[1], p1 = a[3], p2 = a[5], p3 = a[7];
   a[0] = eadd(e0, p0); a[4] = esub(e0, p0);
   a[1] = eadd(e1, p1); a[5] = esub(e1, p1);
-  a[2] = eadd(e2, p2); a[6] = esub(e2, p2);
+  a[2] = add_rot<SIGN>(e2, p2); a[6] = sub_rot<SIGN>(e2, p2);
   a[3] = eadd(e3, p3); a[7] = esub(e3, p3);
 }
 

@@ -241,10 +241,8 @@ __device__ __forceinline__ void interp_pair(const cpair<T>* Y, int K, int mfl, c
 #pragma unroll
   for (int l = 0; l < J; ++l) {
     const cpair<T> y = Y[prow((m0 + l) & (K - 1))];
-    a1.x = fma(c[l], y.a.x, a1.x);
-    a1.y = fma(c[l], y.a.y, a1.y);
-    a2.x = fma(c[l], y.b.x, a2.x);
-    a2.y = fma(c[l], y.b.y, a2.y);
+    a1 = cfma_r(c[l], y.a, a1);
+    a2 = cfma_r(c[l], y.b, a2);
   }
 }
 
@@ -330,10 +328,8 @@ __device__ __forceinline__ void add_sample(const AxArgs<T>& A, cpair<T>* Y, int 
   for (int l = 0; l < J; ++l) {
     const int bi = prow((m0 + l) & (K - 1));
     V y = Y[bi];
-    y.a.x = fma(c[l], v.a.x, y.a.x);
-    y.a.y = fma(c[l], v.a.y, y.a.y);
-    y.b.x = fma(c[l], v.b.x, y.b.x);
-    y.b.y = fma(c[l], v.b.y, y.b.y);
+    y.a = cfma_r(c[l], v.a, y.a);
+    y.b = cfma_r(c[l], v.b, y.b);
     Y[bi] = y;
   }
 }
