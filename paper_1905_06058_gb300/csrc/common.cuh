@@ -41,6 +41,22 @@ template <typename C> __host__ __device__ __forceinline__ C cmulc(C a, C b) {
   C r; r.x = a.x * b.x + a.y * b.y; r.y = a.y * b.x - a.x * b.y; return r;
 }
 template <typename C, typename T> __host__ __device__ __forceinline__ C cscale(C a, T s) { a.x *= s; a.y *= s; return a; }
+// FP32 product and scaling as packed two-lane multiplies / FMAs
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+  const float2 p = __fmul2_rn(a, make_float2(b.x, b.x));                // (a.x b.x, a.y b.x)
+  return __ffma2_rn(make_float2(-a.y, a.x), make_float2(b.y, b.y), p);
+#else
+  float2 r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
+#endif
+}
+__host__ __device__ __forceinline__ float2 cscale(float2 a, float s) {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+  return __fmul2_rn(a, make_float2(s, s));
+#else
+  a.x *= s; a.y *= s; return a;
+#endif
+}
 template <typename C> __host__ __device__ __forceinline__ C cconj(C a) { a.y = -a.y; return a; }
 // acc + c y for a real c
 template <typename C, typename T> __device__ __forceinline__ C cfma_r(T c, C y, C acc) {
