@@ -234,16 +234,16 @@ KERNEL_SOURCES = {
 }
 NCU_CAPTURES = {
     "bscan_1024x2048": {
-        "ax_fused": {"sha": "c4b631adffaf9283", "dram": 42434304, "table": 16809984,
-                     "smem_wavefronts": 6616636},
-        "lat_update": {"sha": "cd9416c519db2f3f", "dram": 34451200, "table": 0,
-                       "smem_wavefronts": 2375502},
+        "ax_fused": {"sha": "684a502d8dcb47ee", "dram": 42545920, "table": 16809984,
+                     "smem_wavefronts": 6614780},
+        "lat_update": {"sha": "f51bff69804d1b72", "dram": 34303488, "table": 0,
+                       "smem_wavefronts": 2417035},
     },
     "volume_256x256x2048": {
-        # 128 x 128 x 2048 capture with the plan's Stolt table: 782,257,152 B and
-        # 116,306,560 wavefronts over 8,194 pairs
-        "ax_fused": {"sha": "c4b631adffaf9283", "dram": 3128455806, "table": 545292288,
-                     "smem_wavefronts": 465141075},
+        # 128 x 128 x 2048 capture with the plan's Stolt table: 781,984,512 B and
+        # 116,490,007 wavefronts over 8,194 pairs
+        "ax_fused": {"sha": "684a502d8dcb47ee", "dram": 3127365445, "table": 545292288,
+                     "smem_wavefronts": 465874728},
     },
 }
 
