@@ -267,6 +267,37 @@ def test_full_bscan_first_iterate_sampled(torch):
     plan.close()
 
 
+@pytest.mark.slow
+def test_full_volume_first_iterate_sampled(torch):
+    """256 x 256 x 2048 volume, benchmarked launch configuration (fused axial
+    kernel with the Stolt table, y-axis update, x-axis passes): after one
+    iteration z^1 = T_{lambda/L}(A^H s / L) (Alg. 1 from eta^1 = 0); three depth
+    planes against the oracle's exact adjoint, a sum over every (q, k)."""
+    import math
+    from paper_1905_06058_gb300.isam import Plan
+    wl = I.config3(dtype=np.complex64)
+    g = wl.geom
+    y = I.random_spectra((g.ny, g.nx, g.nk), 9).astype(np.float32)
+    plan = Plan(g)
+    L, lam = 1.3, 0.05
+    out, info = plan.solve(dev(torch, y, np.float32), lambda_abs=lam, L=L, max_iter=1)
+    rows = np.array([3, 1024, 2000])
+    z = out[:, :, torch.from_numpy(rows).cuda()].cpu().numpy()
+    del out
+    plan.close()
+    ref = O.IsamOracle(g, "exact")
+    gr = ref.grid
+    R = O.lateral_fft(y.astype(np.float64).astype(complex)) * np.conj(ref.phase) * ref.prop
+    G = np.zeros((g.ny, g.nx, rows.size), complex)
+    for i, r in enumerate(rows):
+        for iy in range(0, g.ny, 32):
+            E = np.exp(1j * gr.z[r] * ref.beta[iy:iy + 32])
+            G[iy:iy + 32, :, i] = np.einsum("yxk,yxk->yx", R[iy:iy + 32], E)
+    G /= math.sqrt(gr.nz)
+    z_ref = O.soft_threshold(O.lateral_ifft(G) / L, lam / L)
+    assert rel(z, z_ref) < 3e-5
+
+
 @pytest.mark.parametrize("prec,tol", [("fp32", 1e-3), ("fp64", 1e-6)])
 def test_volume_fista_matches_oracle(torch, prec, tol):
     """3-D (2-D lateral FFT, Stolt map in q_x, q_y): the fused residual uses the
