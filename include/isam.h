@@ -304,8 +304,9 @@ isam_status isam_fista_unrolled_vjp(isam_plan* plan, const void* s_d,
  * info[i] (nullable; rr = -1); returns the first non-OK entry status.  The
  * caller orders earlier work on s_d before the run (e.g. synchronises).
  * The graph records the plans' tables and launch shapes: while a batch
- * exists, isam_set_model, isam_set_filter and isam_autotune on its plans
- * return ISAM_ERR_INVALID, and the plans must not be destroyed. */
+ * exists, isam_set_model, isam_set_filter, isam_autotune, isam_autotune_ex
+ * and isam_set_tuning on its plans return ISAM_ERR_INVALID, and the plans must
+ * not be destroyed. */
 typedef struct isam_batch isam_batch;
 isam_status isam_batch_create(isam_plan* const* plans, int32_t n, const void* const* s_d,
                               const isam_solve_opts* opts, void* const* eta_out, void* stream,

@@ -114,7 +114,8 @@ def test_batch_pins_its_plans(torch):
     p, sd, res, kw = ents[0][:4]
     b = Batch([(e[0], e[1], e[2], e[3]) for e in ents])
     g = ents[0][4].geom
-    for call in (lambda: p.set_model(g.disp, g.z0), lambda: p.set_filter(None), p.autotune):
+    for call in (lambda: p.set_model(g.disp, g.z0), lambda: p.set_filter(None), p.autotune,
+                 lambda: p.set_tuning(axial_radix=8)):
         with pytest.raises(IsamError) as e:
             call()
         assert e.value.status == 1
