@@ -99,7 +99,10 @@ typedef struct {
   int32_t check_every;      /* iterations between stop-rule evaluations (>= 1);   */
                             /* an evaluating iteration reads z^{k-2} as well and   */
                             /* forms the norm partials, the others update from the */
-                            /* lateral spectrum of eta^k - g/L (same iterates)     */
+                            /* lateral spectrum of eta^k - g/L (same iterates).    */
+                            /* r_r is evaluated on the device and read by the host */
+                            /* two iterations later: a solve that stops has queued */
+                            /* up to two more, whose kernels write nothing         */
   const void* w_dev;        /* nullable device [nz] weights w (real, plan type)   */
   int32_t residual_addback; /* 1: return z + (1/L) A^H (s_d - A z) (Alg. 1 end)   */
   double L;                 /* step 1/L; 0: power-iteration estimate, cached      */

@@ -91,6 +91,10 @@ template <typename T> struct LatArgs {
   // FP32 compile-time tiles at L = 1024 and 256: 1 runs the column-split
   // radix-16 transforms, 0 the radix-8 column-pair ones; ignored elsewhere
   int radix16;
+  // solve with the device-side stop rule (see StopRule): a nonzero *stop, read
+  // after the wait for the previous kernel, makes the launch return at once;
+  // null elsewhere
+  const int* stop;
 };
 
 // Columns q and -q share the Stolt map; the axial kernels process them as a
@@ -114,6 +118,8 @@ template <typename T> struct AxArgs {
   // FP32, K = 2048 or 4096: 1 runs the column-split radix-16 transforms, 0 the
   // radix-8 column-pair ones (the plan's tuned choice); ignored elsewhere
   int radix16;
+  // fused kernel in a solve with the device-side stop rule: as LatArgs::stop
+  const int* stop;
 };
 
 // launchers (return cudaGetLastError())
@@ -136,7 +142,19 @@ template <typename T> cudaError_t launch_max_abs(const cplx<T>* x, size_t n, dou
                                                   int nblocks, double* out, cudaStream_t s);
 template <typename T> cudaError_t launch_norm2(const cplx<T>* x, size_t n, double* partial,
                                                 int nblocks, double* out, cudaStream_t s);
-cudaError_t launch_sum3(const double* partial, int n, double* out, cudaStream_t s);
+// The stop rule of Eq. 15 evaluated on the device by the reduction of a
+// check iteration: r_r = ||z - eta|| / (max(||g/L||, ||z - eta + g/L||) + eps)
+// from the three sums, written to *rr; when r_r < tol, stop[0] = 1 and
+// stop[1] = iter.  Once stop[0] is set, later checks (whose partials were not
+// written) leave everything as it is.  stop null: the plain sums only.
+struct StopRule {
+  int* stop;       // [2] device: stopped flag, iteration of the stop
+  double* rr;      // device: r_r of the latest evaluated check
+  double tol, eps;
+  int iter;
+};
+cudaError_t launch_sum3(const double* partial, int n, double* out, const StopRule& sr,
+                        cudaStream_t s);
 template <typename T> cudaError_t launch_wl1(const cplx<T>* x, size_t n, const T* w, int nz,
                                              double* partial, int nblocks, double* out,
                                              cudaStream_t s);

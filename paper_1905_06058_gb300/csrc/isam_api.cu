@@ -69,6 +69,12 @@ struct isam_plan {
   double* dscal = nullptr;      // device scalars [8]
   double* hscal = nullptr;      // pinned host mirror [8]
   int* flag = nullptr;          // device non-finite flag
+  // device-side stop rule of the solve: [stopped, iteration] on the device,
+  // pinned mirrors of the pending check's outcome [0, 2) and of the final one
+  // [2, 4), and an event after the pending check's copy
+  int* dstop = nullptr;
+  int* hstop = nullptr;
+  cudaEvent_t ev_check = nullptr;
   double L_cache = 0.0;
   // autotuned choices (0: the built-in heuristics): lateral update tile width
   // and whether the fused kernel reads the Stolt table (1) or evaluates (2)
@@ -487,13 +493,19 @@ template <typename T> isam_status fista_iteration(isam_plan* P, Impl<T>& im,
                                                   double lam_scale = 0.0,
                                                   int prior = ISAM_PRIOR_L1,
                                                   int prior_iters = 0,
-                                                  cplx<T>* s_out = nullptr) {
+                                                  cplx<T>* s_out = nullptr,
+                                                  const int* stop = nullptr,
+                                                  const StopRule* stop_rule = nullptr) {
   cudaStream_t s = P->stream;
   if (!ehat_in) ehat_in = im.eta_hat;
   if (!ehat_out) ehat_out = im.eta_hat;
+  // device-side stop rule (l1 prior): with stop set, every kernel of the
+  // iteration writes nothing when an earlier check has stopped the solve;
+  // stop_rule: the check iteration's reduction evaluates Eq. 15 (StopRule)
   AxArgs<T> ax = ax_args<T>(P, im, ehat_in, im.grad);
   ax.sdh = im.sdh;
   ax.s_out = s_out;
+  ax.stop = stop;
   // l1 iterations without the residual check: the fused kernel writes the
   // lateral spectrum of u = eta^k - g/L (u_hat = eta_hat^k - G/L, linear in
   // both), so the update needs z^{k-1} only, not z^{k-2} to rebuild eta^k.
@@ -560,9 +572,12 @@ template <typename T> isam_status fista_iteration(isam_plan* P, Impl<T>& im,
   if (P->ny == 1) {
     u = lat_args<T>(1, P->nx, P->nz, im.grad, ehat_out);
   } else {
-    ISAM_TRY(lat<T>(P, LAT_C2C_INV, lat_args<T>(P->ny, P->nx, P->nz, im.grad, im.grad)));
+    LatArgs<T> x = lat_args<T>(P->ny, P->nx, P->nz, im.grad, im.grad);
+    x.stop = stop;
+    ISAM_TRY(lat<T>(P, LAT_C2C_INV, x));
     u = lat_args<T>(1, P->ny, P->nx * P->nz, im.grad, ehat_out);
   }
+  u.stop = stop;
   if (P->tune_tp) {
     u.TZ = P->tune_tp;
     u.logTZ = ilog2(P->tune_tp);
@@ -575,10 +590,16 @@ template <typename T> isam_status fista_iteration(isam_plan* P, Impl<T>& im,
   ISAM_TRY(lat<T>(P, from_u ? LAT_UPDATE_U : LAT_UPDATE, u));
   if (norms) {
     const int nblk = (u.M / (2 * u.TZ)) * u.B;
-    ISAM_TRY(launch(P, ISAM_KCLASS_MISC, [&] { return launch_sum3(P->partial, nblk, P->dscal + 1, s); }));
+    const StopRule sr = stop_rule ? *stop_rule : StopRule{};
+    ISAM_TRY(launch(P, ISAM_KCLASS_MISC, [&] {
+      return launch_sum3(P->partial, nblk, P->dscal + 1, sr, s);
+    }));
   }
-  if (P->ny > 1)
-    ISAM_TRY(lat<T>(P, LAT_C2C_FWD, lat_args<T>(P->ny, P->nx, P->nz, ehat_out, ehat_out)));
+  if (P->ny > 1) {
+    LatArgs<T> x = lat_args<T>(P->ny, P->nx, P->nz, ehat_out, ehat_out);
+    x.stop = stop;
+    ISAM_TRY(lat<T>(P, LAT_C2C_FWD, x));
+  }
   return ISAM_OK;
 }
 
@@ -653,22 +674,60 @@ template <typename T> isam_status solve_impl(isam_plan* P, const T* s_d, const i
   const double eps = o->eps > 0 ? o->eps : 1e-30;
   double rr = -1.0;
   int done = 0;
+  // The stop rule runs on the device (StopRule; only the l1 prior takes
+  // tol > 0).  The host reads a check's outcome kStopLag iterations after
+  // queuing it, so a check never drains the GPU; only the iterations queued
+  // while an outcome is unread carry the stop flag (their kernels write nothing
+  // once it is set), and the result is the iterate of the stopping check.
+  constexpr int kStopLag = 2;
+  const bool dev_stop = check;
+  if (dev_stop) CUDA_TRY(cudaMemsetAsync(P->dstop, 0, 2 * sizeof(int), s));
+  bool pending = false;   // a check whose outcome the host has not read
+  int since = 0;          // iterations queued after it
   for (int it = 1; it <= o->max_iter; ++it) {
     const int k = k0 + it;
     const bool norms = check && (it % every == 0 || it == o->max_iter);
+    StopRule sr{};
+    if (dev_stop) {
+      sr.stop = P->dstop;
+      sr.rr = P->dscal + 7;
+      sr.tol = o->tol;
+      sr.eps = eps;
+      sr.iter = it;
+    }
     ISAM_TRY(fista_iteration<T>(P, im, zP, zQ, zQ, static_cast<const T*>(o->w_dev), lam, L,
                                 mu[k - 1], mu[k], norms, nullptr, nullptr, nullptr, nullptr, 0.0,
-                                o->prior, o->prior_iters));
+                                o->prior, o->prior_iters, nullptr, pending ? P->dstop : nullptr,
+                                dev_stop && norms ? &sr : nullptr));
     std::swap(zP, zQ);   // zP = z^k, zQ = z^{k-1}
     done = it;
-    if (norms) {
-      CUDA_TRY(cudaMemcpyAsync(P->hscal + 1, P->dscal + 1, 3 * sizeof(double),
-                               cudaMemcpyDeviceToHost, s));
-      CUDA_TRY(cudaStreamSynchronize(s));
-      harvest_events(P);
-      const double a = sqrt(P->hscal[1]), g = sqrt(P->hscal[2]), b = sqrt(P->hscal[3]);
-      rr = a / (std::max(g, b) + eps);
-      if (rr < o->tol) break;
+    if (dev_stop) {
+      // read the pending check once kStopLag iterations keep the GPU busy, or
+      // before this check's outcome takes the pinned slot
+      if (pending && (++since >= kStopLag || norms)) {
+        CUDA_TRY(cudaEventSynchronize(P->ev_check));
+        pending = false;
+        if (P->hstop[0]) break;
+      }
+      if (norms) {
+        CUDA_TRY(cudaMemcpyAsync(P->hstop, P->dstop, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaEventRecord(P->ev_check, s));
+        pending = true;
+        since = 0;
+      }
+    }
+  }
+  if (dev_stop) {
+    // where the device stopped (if it did) and r_r of that check, else of the last
+    CUDA_TRY(cudaMemcpyAsync(P->hstop + 2, P->dstop, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(P->hscal + 7, P->dscal + 7, sizeof(double), cudaMemcpyDeviceToHost,
+                             s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    rr = P->hscal[7];
+    if (P->hstop[2]) {
+      const int stop_it = P->hstop[3];
+      if ((done - stop_it) & 1) std::swap(zP, zQ);   // z^{stop_it} and z^{stop_it - 1}
+      done = stop_it;
     }
   }
   // objective of Eq. 12 at z^K
@@ -944,6 +1003,9 @@ isam_status isam_plan_create(const isam_params* p, void* stream, isam_plan** out
   if (st == ISAM_OK) st = dalloc(&P->dscal, 8);
   if (st == ISAM_OK) st = dalloc(&P->flag, 1);
   if (st == ISAM_OK) st = from_cuda(cudaMallocHost(reinterpret_cast<void**>(&P->hscal), 8 * sizeof(double)));
+  if (st == ISAM_OK) st = dalloc(&P->dstop, 2);
+  if (st == ISAM_OK) st = from_cuda(cudaMallocHost(reinterpret_cast<void**>(&P->hstop), 4 * sizeof(int)));
+  if (st == ISAM_OK) st = from_cuda(cudaEventCreateWithFlags(&P->ev_check, cudaEventDisableTiming));
   if (st == ISAM_OK) st = build_pairs(P);
   if (st == ISAM_OK) st = build_poly(P);
   if (st == ISAM_OK) {
@@ -970,7 +1032,10 @@ void isam_plan_destroy(isam_plan* P) {
   dfree(P->pairs);
   dfree(P->dscal);
   dfree(P->flag);
+  dfree(P->dstop);
   if (P->hscal) cudaFreeHost(P->hscal);
+  if (P->hstop) cudaFreeHost(P->hstop);
+  if (P->ev_check) cudaEventDestroy(P->ev_check);
   harvest_events(P);
   for (cudaEvent_t e : P->ev_pool) cudaEventDestroy(e);
   delete P;

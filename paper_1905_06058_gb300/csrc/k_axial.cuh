@@ -600,6 +600,10 @@ __global__ void __launch_bounds__(512, 2) k_ax_fused(const __grid_constant__ AxA
   cudaTriggerProgrammaticLaunchCompletion();
   ax_twiddles<T, LOGK, C16>(tw, sc);
   cudaGridDependencySynchronize();
+  // the solve's stop flag (written by an earlier kernel, so visible after the
+  // wait): loaded here, tested after the forward transform (before the first
+  // global write), so its latency overlaps the transform
+  const bool stopped = A.stop != nullptr && __ldcg(A.stop) != 0;
   // F s_d at this pair's samples, fetched before the transforms need them (the
   // column-split transforms take them after the forward transform: their
   // registers are needed there)
@@ -613,6 +617,7 @@ __global__ void __launch_bounds__(512, 2) k_ax_fused(const __grid_constant__ AxA
     }
   }
   ax_forward<T, LOGK, C16>(A, Y, tw, c1, c2, two);
+  if (stopped) return;   // an earlier check stopped the solve: write nothing
   if constexpr (COL16) {
 #pragma unroll
     for (int rho = 0; rho < NRES; ++rho) {

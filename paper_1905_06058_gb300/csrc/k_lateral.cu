@@ -101,6 +101,10 @@ __global__ void __launch_bounds__(512, 2) k_lat(const __grid_constant__ LatArgs<
   if constexpr (COL16) c16::build_lat_twiddles<LOGL>(reinterpret_cast<float4*>(tw));
   else build_twiddles<T>(tw, L, CT ? LOGL : a.logL, CT ? 0 : a.r3);
   cudaGridDependencySynchronize();
+  // the solve's stop flag (written by an earlier kernel, so visible after the
+  // wait): loaded here, tested before the first global write (after the first
+  // transform), so its latency overlaps the tile's loads
+  const bool stopped = a.stop != nullptr && __ldcg(a.stop) != 0;
   const int col = tid & (TP - 1), b = tid >> logTP;
   const size_t M = size_t(a.M);
   const size_t m_first = size_t(blockIdx.x) * (2 * TP);
@@ -152,6 +156,7 @@ __global__ void __launch_bounds__(512, 2) k_lat(const __grid_constant__ LatArgs<
 
   if (MODE == LAT_C2C_FWD || MODE == LAT_R2C_FWD || MODE == LAT_EXTRAP_FWD) lat_fft(FWD{});
   else lat_fft(INV{});
+  if (stopped) return;   // an earlier check stopped the solve: write nothing
 
   const T nrm = a.norm;
   if (MODE == LAT_C2C_FWD || MODE == LAT_C2C_INV || MODE == LAT_R2C_FWD ||

@@ -126,20 +126,30 @@ __global__ void __launch_bounds__(256) k_reduce1(const cplx<T>* x, size_t n, dou
   }
 }
 
+// One block of 256 threads combines values in a fixed order: every thread its
+// strided share, then a shuffle tree within each warp and across the eight
+// warps' results (the same order on every run; no serial chain of 256 adds).
+template <bool MAX> __device__ __forceinline__ double combine(double a, double b) {
+  return MAX ? nan_max(a, b) : a + b;
+}
+template <bool MAX> __device__ __forceinline__ double block256_combine(double v, double* red8) {
+  for (int o = 16; o > 0; o >>= 1) v = combine<MAX>(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) red8[threadIdx.x >> 5] = v;
+  __syncthreads();
+  v = threadIdx.x < 8 ? red8[threadIdx.x] : 0.0;
+  if (threadIdx.x < 32)
+    for (int o = 4; o > 0; o >>= 1) v = combine<MAX>(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;   // the block's result in thread 0
+}
+
 // single block: out = sqrt(max or sum of partial)
 template <bool MAX>
 __global__ void __launch_bounds__(256) k_reduce2(const double* partial, int n, double* out) {
-  __shared__ double red[256];
+  __shared__ double red[8];
   double v = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x)
-    v = MAX ? nan_max(v, partial[i]) : v + partial[i];
-  red[threadIdx.x] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int i = 0; i < int(blockDim.x); ++i) t = MAX ? nan_max(t, red[i]) : t + red[i];
-    *out = sqrt(t);
-  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v = combine<MAX>(v, partial[i]);
+  v = block256_combine<MAX>(v, red);
+  if (threadIdx.x == 0) *out = sqrt(v);
 }
 
 template <typename T> cudaError_t launch_max_abs(const cplx<T>* x, size_t n, double* partial,
@@ -182,16 +192,11 @@ __global__ void __launch_bounds__(256) k_wl1(const cplx<T>* x, size_t n, const T
   }
 }
 __global__ void __launch_bounds__(256) k_sum1(const double* partial, int n, double* out) {
-  __shared__ double red[256];
+  __shared__ double red[8];
   double v = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) v += partial[i];
-  red[threadIdx.x] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int i = 0; i < int(blockDim.x); ++i) t += red[i];
-    *out = t;
-  }
+  v = block256_combine<false>(v, red);
+  if (threadIdx.x == 0) *out = v;
 }
 template <typename T> cudaError_t launch_wl1(const cplx<T>* x, size_t n, const T* w, int nz,
                                              double* partial, int nblocks, double* out,
@@ -206,21 +211,33 @@ template cudaError_t launch_wl1<double>(const double2*, size_t, const double*, i
                                         double*, cudaStream_t);
 
 // out[0..2] = column sums of partial[n][3]
-__global__ void __launch_bounds__(256) k_sum3(const double* partial, int n, double* out) {
-  __shared__ double red[3][256];
+__global__ void __launch_bounds__(256) k_sum3(const double* partial, int n, double* out,
+                                              const StopRule sr) {
+  __shared__ double red[3][8];
+  // an earlier check stopped the solve: this iteration's kernels returned
+  // without writing the partials
+  if (sr.stop && *reinterpret_cast<const volatile int*>(sr.stop)) return;
   double v[3] = {0.0, 0.0, 0.0};
   for (int i = threadIdx.x; i < n; i += blockDim.x)
     for (int c = 0; c < 3; ++c) v[c] += partial[3 * i + c];
-  for (int c = 0; c < 3; ++c) red[c][threadIdx.x] = v[c];
-  __syncthreads();
-  if (threadIdx.x < 3) {
-    double t = 0.0;
-    for (int i = 0; i < int(blockDim.x); ++i) t += red[threadIdx.x][i];
-    out[threadIdx.x] = t;
+  for (int c = 0; c < 3; ++c) v[c] = block256_combine<false>(v[c], red[c]);
+  if (threadIdx.x == 0) {
+    for (int c = 0; c < 3; ++c) out[c] = v[c];
+    if (sr.stop) {
+      // Eq. 15 as the host evaluates it (the larger of the two norms, NaN kept)
+      const double a = sqrt(v[0]), g = sqrt(v[1]), b = sqrt(v[2]);
+      const double rr = a / ((g < b ? b : g) + sr.eps);
+      *sr.rr = rr;
+      if (rr < sr.tol) {
+        sr.stop[1] = sr.iter;
+        sr.stop[0] = 1;
+      }
+    }
   }
 }
-cudaError_t launch_sum3(const double* partial, int n, double* out, cudaStream_t s) {
-  k_sum3<<<1, 256, 0, s>>>(partial, n, out);
+cudaError_t launch_sum3(const double* partial, int n, double* out, const StopRule& sr,
+                        cudaStream_t s) {
+  k_sum3<<<1, 256, 0, s>>>(partial, n, out, sr);
   return cudaGetLastError();
 }
 

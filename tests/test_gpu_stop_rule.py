@@ -72,3 +72,29 @@ def test_stop_rule_small_lateral_blocks(torch, case, prec):
             assert info["rr"] == pytest.approx(res.rr, rel=1e-3)
             assert rel(out.cpu().numpy(), res.eta) < 1e-3
         assert info["rr"] < 1e-3
+
+
+@pytest.mark.parametrize("ny", [1, 4], ids=["bscan", "volume"])
+def test_device_stop_returns_the_stopping_iterate(torch, ny):
+    """The stop rule runs on the device and the host queues a further check
+    interval before it reads a check's outcome; kernels queued past the stop
+    return at once.  So a solve that stops at check k returns exactly (bit for
+    bit) the iterate, count and r_r of a solve with the same checks that ends
+    at iteration k."""
+    from paper_1905_06058_gb300.isam import Plan
+    wl = I.small_bscan(nx=16, ny=ny, nk=64, nz=64, n_points=6, seed=23)
+    ref = O.IsamOracle(wl.geom, "nufft")
+    s = ref.forward(wl.eta)
+    plan = Plan(wl.geom, precision="fp32", stolt_table=False)
+    sd = torch.from_numpy(s.astype(np.float32)).cuda()
+    kw = dict(lambda_rel=0.05, L=4.0, check_every=10)
+    # r_r at iteration 20, then a tolerance the rule meets at check 10 or 20
+    _, probe = plan.solve(sd, max_iter=20, tol=1e-300, **kw)
+    z, info = plan.solve(sd, max_iter=200, tol=probe["rr"] * 1.0001, **kw)
+    k = info["iterations"]
+    assert k in (10, 20)
+    z_ref, info_ref = plan.solve(sd, max_iter=k, tol=1e-300, **kw)
+    assert info_ref["iterations"] == k
+    assert info["rr"] == info_ref["rr"]
+    assert torch.equal(z, z_ref)
+    plan.close()
