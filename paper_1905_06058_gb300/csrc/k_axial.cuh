@@ -505,7 +505,10 @@ __global__ void __launch_bounds__(512) k_ax_fwd(const __grid_constant__ AxArgs<T
   int c1, c2, mx, my;
   pair_columns(A, c1, c2, mx, my);
   const bool two = c2 != c1;
+  // programmatic dependent launch (as k_ax_fused): twiddles before the wait
+  cudaTriggerProgrammaticLaunchCompletion();
   ax_twiddles<T, LOGK, C16>(tw, sc);
+  cudaGridDependencySynchronize();
   ax_forward<T, LOGK, C16>(A, Y, tw, c1, c2, two);
 
   const Positions<T> pos(A, mx, my);
@@ -543,7 +546,10 @@ __global__ void __launch_bounds__(512, 2) k_ax_adj(const __grid_constant__ AxArg
   pair_columns(A, c1, c2, mx, my);
   const bool two = c2 != c1;
   if (tid == 0) { ch_lo = INT_MAX; ch_hi = INT_MIN; }
+  // programmatic dependent launch (as k_ax_fused): twiddles before the wait
+  cudaTriggerProgrammaticLaunchCompletion();
   ax_twiddles<T, LOGK, C16>(tw, sc);
+  cudaGridDependencySynchronize();
   const Positions<T> pos(A, mx, my);
   const C* r1 = A.in + size_t(c1) * nk;
   const C* r2 = A.in + size_t(c2) * nk;
@@ -712,31 +718,24 @@ static cudaError_t launch_ax_JKC(const AxArgs<T>& a, int npairs, cudaStream_t s,
   const int K = a.sc.K;
   const int threads = K / 8;
   const size_t sm = ax_smem_bytes<T>(K, a.sc.nk, kind != AX_FWD);
-  if (kind == AX_ADJ) {
-    auto* kern = k_ax_adj<T, J, LOGK, C16>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-    kern<<<npairs, threads, sm, s>>>(a);
-  } else if (kind == AX_FWD) {
-    auto* kern = k_ax_fwd<T, J, LOGK, C16>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-    kern<<<npairs, threads, sm, s>>>(a);
-  } else {
-    auto* kern = a.s_out ? k_ax_fused<T, J, LOGK, true, C16> : k_ax_fused<T, J, LOGK, false, C16>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-    // programmatic dependent launch (see k_ax_fused's prologue)
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(npairs);
-    cfg.blockDim = dim3(threads);
-    cfg.dynamicSmemBytes = sm;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, a);
-  }
-  return cudaGetLastError();
+  void (*kern)(AxArgs<T>);
+  if (kind == AX_ADJ) kern = k_ax_adj<T, J, LOGK, C16>;
+  else if (kind == AX_FWD) kern = k_ax_fwd<T, J, LOGK, C16>;
+  else kern = a.s_out ? k_ax_fused<T, J, LOGK, true, C16> : k_ax_fused<T, J, LOGK, false, C16>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+  // programmatic dependent launch: each axial kernel builds its twiddles while
+  // the previous kernel finishes, then waits for it (cudaGridDependencySynchronize)
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(npairs);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
 // the plan's radix choice (a.radix16) where both forms exist
