@@ -234,16 +234,16 @@ KERNEL_SOURCES = {
 }
 NCU_CAPTURES = {
     "bscan_1024x2048": {
-        "ax_fused": {"sha": "684a502d8dcb47ee", "dram": 42545920, "table": 16809984,
-                     "smem_wavefronts": 6614780},
-        "lat_update": {"sha": "f51bff69804d1b72", "dram": 34303488, "table": 0,
-                       "smem_wavefronts": 2417035},
+        "ax_fused": {"sha": "057b638d1b9bcc4b", "dram": 42470144, "table": 16809984,
+                     "smem_wavefronts": 6627047},
+        "lat_update": {"sha": "6679ff124393cb1f", "dram": 34274048, "table": 0,
+                       "smem_wavefronts": 2411818},
     },
     "volume_256x256x2048": {
-        # 128 x 128 x 2048 capture with the plan's Stolt table: 781,984,512 B and
-        # 116,490,007 wavefronts over 8,194 pairs
-        "ax_fused": {"sha": "684a502d8dcb47ee", "dram": 3127365445, "table": 545292288,
-                     "smem_wavefronts": 465874728},
+        # 128 x 128 x 2048 capture with the plan's Stolt table: 781,804,288 B and
+        # 116,585,738 wavefronts over 8,194 pairs
+        "ax_fused": {"sha": "057b638d1b9bcc4b", "dram": 3126644681, "table": 545292288,
+                     "smem_wavefronts": 466257583},
     },
 }
 
