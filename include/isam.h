@@ -295,9 +295,13 @@ isam_status isam_fista_unrolled_vjp(isam_plan* plan, const void* s_d,
  * dispersion, focus), data, lambda, L, weights and iteration count, recorded
  * once into one CUDA graph; isam_batch_run replays the whole batch with one
  * launch.  Each entry runs on its own forked stream, so entries overlap on
- * the GPU; one entry is the same kernel sequence as isam_solve with tol = 0.
- * Create: plans distinct, on one device, profiling off; opts[i].tol must be 0
- * (the stop rule needs the host); L = 0 is estimated now (cached per plan);
+ * the GPU; one entry is the same kernel sequence as isam_solve.  With
+ * opts[i].tol > 0 the stop rule runs on the device: every iteration after the
+ * first check carries the stop flag (its kernels write nothing once the rule
+ * has fired), eta_out[i] receives the iterate of the stopping check, and
+ * isam_batch_run reports that check's iteration and r_r.
+ * Create: plans distinct, on one device, profiling off; L = 0 is estimated now
+ * (cached per plan);
  * lambda_rel is evaluated on the device at every run from the s_d[i] contents
  * then.  The batch keeps the pointers: plans, s_d[i] (device spectra) and
  * eta_out[i] (device images) must stay valid, and the plans unused by other

@@ -155,6 +155,12 @@ struct StopRule {
 };
 cudaError_t launch_sum3(const double* partial, int n, double* out, const StopRule& sr,
                         cudaStream_t s);
+// out = the iterate of the stopping check: the two iterate buffers alternate,
+// so z^{stop[1]} is in a (z^last) when last - stop[1] is even, else in b; a
+// solve that did not stop (stop[0] == 0) returns a
+template <typename T> cudaError_t launch_select_iterate(const cplx<T>* a, const cplx<T>* b,
+                                                         cplx<T>* out, size_t n, const int* stop,
+                                                         int last, cudaStream_t s);
 template <typename T> cudaError_t launch_wl1(const cplx<T>* x, size_t n, const T* w, int nz,
                                              double* partial, int nblocks, double* out,
                                              cudaStream_t s);

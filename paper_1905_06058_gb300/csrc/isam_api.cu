@@ -1593,6 +1593,9 @@ template <typename T> isam_status batch_prepare(isam_plan* P, const isam_solve_o
 // One whole solve on the plan's stream with no host synchronisation: the
 // relative lambda = c ||A^H s_d||_inf stays on the device (the update kernel
 // reads it), so a recorded graph stays correct when s_d's contents change.
+// With tol > 0 the stop rule runs on the device (StopRule): every iteration
+// after the first check carries the stop flag, and the output is the iterate
+// of the stopping check (launch_select_iterate).
 template <typename T> isam_status batch_enqueue(isam_plan* P, const T* s_d,
                                                 const isam_solve_opts* o, double L,
                                                 cplx<T>* eta_out) {
@@ -1621,21 +1624,43 @@ template <typename T> isam_status batch_enqueue(isam_plan* P, const T* s_d,
   cplx<T>* zP = im.zA;
   cplx<T>* zQ = im.zB;
   const T* w = static_cast<const T*>(o->w_dev);
+  const bool check = o->tol > 0;
+  const int every = std::max(1, o->check_every);
+  const int first_check = std::min(every, o->max_iter);
+  if (check) CUDA_TRY(cudaMemsetAsync(P->dstop, 0, 2 * sizeof(int), s));
   for (int k = 1; k <= o->max_iter; ++k) {
-    ISAM_TRY(fista_iteration<T>(P, im, zP, zQ, zQ, w, lam, L, mu[k - 1], mu[k], false, nullptr,
-                                nullptr, nullptr, lam_dev, lam_scale, o->prior, o->prior_iters));
+    const bool norms = check && (k % every == 0 || k == o->max_iter);
+    StopRule sr{};
+    sr.stop = P->dstop;
+    sr.rr = P->dscal + 7;
+    sr.tol = o->tol;
+    sr.eps = o->eps > 0 ? o->eps : 1e-30;
+    sr.iter = k;
+    ISAM_TRY(fista_iteration<T>(P, im, zP, zQ, zQ, w, lam, L, mu[k - 1], mu[k], norms, nullptr,
+                                nullptr, nullptr, lam_dev, lam_scale, o->prior, o->prior_iters,
+                                nullptr, check && k > first_check ? P->dstop : nullptr,
+                                norms ? &sr : nullptr));
     std::swap(zP, zQ);
   }
+  cplx<T>* z = zP;
+  if (check) {
+    // z^{k_stop} (the last iterate when the rule did not fire) into eta_out;
+    // the add-back below reads it there and updates it in place
+    z = eta_out;
+    ISAM_TRY(launch(P, ISAM_KCLASS_MISC, [&] {
+      return launch_select_iterate<T>(zP, zQ, z, P->n_img, P->dstop, o->max_iter, s);
+    }));
+  }
   if (o->residual_addback) {
-    ISAM_TRY(op_forward<T>(P, zP, im.s_tmp));
+    ISAM_TRY(op_forward<T>(P, z, im.s_tmp));
     ISAM_TRY(launch(P, ISAM_KCLASS_MISC, [&] {
       return launch_rsub<T>(s_d, im.s_tmp, im.s_tmp, P->n_spec, s);
     }));
     ISAM_TRY(op_adjoint<T>(P, im.s_tmp, im.grad));
     ISAM_TRY(launch(P, ISAM_KCLASS_MISC, [&] {
-      return launch_caxpy<T>(zP, im.grad, T(1.0 / L), eta_out, P->n_img, s);
+      return launch_caxpy<T>(z, im.grad, T(1.0 / L), eta_out, P->n_img, s);
     }));
-  } else {
+  } else if (!check) {
     CUDA_TRY(cudaMemcpyAsync(eta_out, zP, bytes, cudaMemcpyDeviceToDevice, s));
   }
   return ISAM_OK;
@@ -1667,7 +1692,6 @@ isam_status isam_batch_create(isam_plan* const* plans, int32_t n, const void* co
   for (int i = 0; i < n; ++i) {
     if (!plans[i] || !s_d[i] || !eta_out[i]) return ISAM_ERR_INVALID;
     ISAM_TRY(check_opts(plans[i], &opts[i]));
-    if (opts[i].tol != 0.0) return ISAM_ERR_INVALID;       // no host stop rule in a graph
     if (plans[i]->prof || plans[i]->device != plans[0]->device) return ISAM_ERR_INVALID;
     for (int j = 0; j < i; ++j)
       if (plans[j] == plans[i]) return ISAM_ERR_INVALID;
@@ -1764,11 +1788,18 @@ isam_status isam_batch_run(isam_batch* B, isam_solve_info* info) {
       CUDA_TRY(cudaMemcpy(&m, P->dscal, sizeof(double), cudaMemcpyDeviceToHost));
       lam = o.lambda_rel * m;
     }
+    // the device-side stop rule's outcome: [stopped, iteration] and r_r
+    int stop[2] = {0, 0};
+    double rr = -1.0;
+    if (o.tol > 0) {
+      CUDA_TRY(cudaMemcpy(stop, P->dstop, 2 * sizeof(int), cudaMemcpyDeviceToHost));
+      CUDA_TRY(cudaMemcpy(&rr, P->dscal + 7, sizeof(double), cudaMemcpyDeviceToHost));
+    }
     const isam_status st = flag ? ISAM_ERR_NONFINITE : ISAM_OK;
     if (st != ISAM_OK && first == ISAM_OK) first = st;
     if (info) {
-      info[i].iterations = o.max_iter;
-      info[i].rr = -1.0;
+      info[i].iterations = stop[0] ? stop[1] : o.max_iter;
+      info[i].rr = rr;
       info[i].lambda = lam;
       info[i].L = B->L[i];
       info[i].status = st;

@@ -242,6 +242,25 @@ cudaError_t launch_sum3(const double* partial, int n, double* out, const StopRul
 }
 
 template <typename T>
+__global__ void k_select_iterate(const cplx<T>* a, const cplx<T>* b, cplx<T>* out, size_t n,
+                                 const int* stop, int last) {
+  const cplx<T>* src = stop[0] != 0 && ((last - stop[1]) & 1) ? b : a;
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += size_t(gridDim.x) * blockDim.x)
+    out[i] = src[i];
+}
+template <typename T> cudaError_t launch_select_iterate(const cplx<T>* a, const cplx<T>* b,
+                                                         cplx<T>* out, size_t n, const int* stop,
+                                                         int last, cudaStream_t s) {
+  k_select_iterate<T><<<1024, 256, 0, s>>>(a, b, out, n, stop, last);
+  return cudaGetLastError();
+}
+template cudaError_t launch_select_iterate<float>(const float2*, const float2*, float2*, size_t,
+                                                  const int*, int, cudaStream_t);
+template cudaError_t launch_select_iterate<double>(const double2*, const double2*, double2*,
+                                                   size_t, const int*, int, cudaStream_t);
+
+template <typename T>
 __global__ void k_scale(cplx<T>* x, size_t n, const double* denom) {
   const double d = *denom;
   const T f = d > 0.0 ? T(1.0 / d) : T(0);

@@ -514,8 +514,9 @@ class Batch:
             sds[i] = plan._dev(s, plan.real_dtype, plan.spec_shape, "s_d")
             outs[i] = plan._dev(out, plan.cplx_dtype, plan.image_shape, "out")
             opts[i] = plan._opts(kw.get("lambda_rel", 0.01), kw.get("lambda_abs", 0.0),
-                                 kw.get("max_iter", 100), 0.0, 1, kw.get("w"),
-                                 kw.get("addback", False), kw.get("L", 0.0), 0.0,
+                                 kw.get("max_iter", 100), kw.get("tol", 0.0),
+                                 kw.get("check_every", 10), kw.get("w"),
+                                 kw.get("addback", False), kw.get("L", 0.0), kw.get("eps", 0.0),
                                  kw.get("prior", "l1"), False, kw.get("prior_iters", 0))
             self._keep.append((plan, s, out, kw.get("w")))
         self.n = n

@@ -5,7 +5,8 @@ count) equals the same plan's isam_solve within 1e-5 (FP32 rounding of
 lambda / L is formed in another order) and one entry matches the oracle's
 FISTA within 1e-3; a replay after overwriting s_d follows the new data (the
 relative lambda is evaluated on the device); bad batches are refused and a
-non-finite entry is reported without touching the others."""
+non-finite entry is reported without touching the others; the stop rule runs
+inside the graph."""
 import numpy as np
 import pytest
 
@@ -70,6 +71,33 @@ def test_batch_matches_individual_solves_and_oracle(torch):
         e[0].close()
 
 
+@pytest.mark.parametrize("addback", [False, True])
+def test_batch_stop_rule(torch, addback):
+    """Alg. 1's stop rule inside the graph (evaluated on the device): every
+    entry stops at the same check as its own isam_solve with the same
+    tolerance, with the same r_r and image (1e-5), and the graph's output is
+    that check's iterate (and its residual add-back), not the last queued one;
+    a replay starts over (the stop flag is reset by the graph)."""
+    from paper_1905_06058_gb300.isam import Batch
+    ents = entries(torch, seed0=90)
+    for i, e in enumerate(ents):
+        e[3].update(max_iter=200, tol=[3e-2, 1e-2, 2e-2, 1e-9][i], check_every=5,
+                    addback=addback)
+    b = Batch([(p, sd, res, kw) for p, sd, res, kw, *_ in ents])
+    for rep in range(2):
+        infos = b.run()
+        for (p, sd, res, kw, *_), info in zip(ents, infos):
+            ref, rinfo = p.solve(sd, **kw)
+            assert info["status"] == 0
+            assert info["iterations"] == rinfo["iterations"]
+            assert info["rr"] == pytest.approx(rinfo["rr"], rel=1e-4)
+            assert rel(res.cpu().numpy(), ref.cpu().numpy()) < 1e-5
+    assert infos[3]["iterations"] == 200 and min(i["iterations"] for i in infos[:3]) < 200
+    b.close()
+    for e in ents:
+        e[0].close()
+
+
 def test_batch_replay_follows_new_data(torch):
     from paper_1905_06058_gb300.isam import Batch
     ents = entries(torch, seed0=60)
@@ -93,12 +121,12 @@ def test_batch_refusals_and_nonfinite_entry(torch):
         Batch([(p, sd, res, kw), (p, sd, res, kw)])          # one plan twice
     import ctypes
     from paper_1905_06058_gb300 import isam as B
-    o = p._opts(0.01, 0.0, 10, 1e-3, 1, None, False, 1.0, 0.0)
+    o = p._opts(0.01, 0.0, 10, -1.0, 1, None, False, 1.0, 0.0)
     h = ctypes.c_void_p()
     arr = (ctypes.c_void_p * 1)(p._h)
     st = B.lib().isam_batch_create(arr, 1, (ctypes.c_void_p * 1)(sd.data_ptr()), ctypes.byref(o),
                                    (ctypes.c_void_p * 1)(res.data_ptr()), None, ctypes.byref(h))
-    assert st == 1 and not h.value                           # tol > 0 refused
+    assert st == 1 and not h.value                           # tol < 0 refused
     ents[1][1][0, 3, 5] = float("nan")
     b = Batch([(p, sd, res, kw) for p, sd, res, kw, *_ in ents])
     infos = b.run()
