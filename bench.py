@@ -234,16 +234,16 @@ KERNEL_SOURCES = {
 }
 NCU_CAPTURES = {
     "bscan_1024x2048": {
-        "ax_fused": {"sha": "057b638d1b9bcc4b", "dram": 42470144, "table": 16809984,
-                     "smem_wavefronts": 6627047},
-        "lat_update": {"sha": "6679ff124393cb1f", "dram": 34274048, "table": 0,
-                       "smem_wavefronts": 2411818},
+        "ax_fused": {"sha": "42f5dcc0e5acc4f1", "dram": 42414080, "table": 16809984,
+                     "smem_wavefronts": 6623241},
+        "lat_update": {"sha": "aa2e880b8cc2d1e4", "dram": 34312448, "table": 0,
+                       "smem_wavefronts": 2414784},
     },
     "volume_256x256x2048": {
-        # 128 x 128 x 2048 capture with the plan's Stolt table: 781,804,288 B and
-        # 116,585,738 wavefronts over 8,194 pairs
-        "ax_fused": {"sha": "057b638d1b9bcc4b", "dram": 3126644681, "table": 545292288,
-                     "smem_wavefronts": 466257583},
+        # 128 x 128 x 2048 capture with the plan's Stolt table: 781,895,936 B and
+        # 116,578,155 wavefronts over 8,194 pairs
+        "ax_fused": {"sha": "42f5dcc0e5acc4f1", "dram": 3127011206, "table": 545292288,
+                     "smem_wavefronts": 466227256},
     },
 }
 
