@@ -497,8 +497,10 @@ class Batch:
     recorded once as one CUDA graph and replayed with one launch.
 
     ``entries`` is a list of (plan, s_d, out, solve keyword dict); the keywords
-    are those of Plan.solve (lambda_rel, lambda_abs, max_iter, w, addback, L).
-    The tensors are kept referenced by the batch."""
+    are those of Plan.solve (lambda_rel, lambda_abs, max_iter, tol, check_every,
+    w, addback, L, eps, prior, prior_iters).  With tol > 0 the stop rule runs
+    on the device inside the graph and run() reports each entry's stopping
+    iteration and r_r.  The tensors are kept referenced by the batch."""
 
     def __init__(self, entries, stream=None):
         self._h = None
